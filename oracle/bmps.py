@@ -1,0 +1,316 @@
+"""CPU oracle for the generalized boundary-MPS contraction and the TNS sampler.
+
+TEST INFRASTRUCTURE ONLY.  complex128 numpy/LAPACK, one sample at a time,
+following the paper's Appendix "Sampling from a Tensor Network State" (Fig. 7):
+
+* partitions are the grid rows b = 0..H-1 (the grid is oriented so that rows
+  are the long direction and the boundary MPS runs along the short side);
+* the norm network is contracted once from the bottom, giving the stored
+  environments E_{b+1} ("M_{b+1 -> b}" in the paper), each an MPS of rank R;
+* each sample sweeps the rows top to bottom: the row is absorbed into the
+  sample's boundary MPS m_b and compressed to rank R ("fit"), the row's qubits
+  are drawn one by one from their one-site conditional marginals, and the
+  projected row becomes m_{b+1};
+* q(x) is the product of the conditionals.
+
+The MPS-MPO compression is a zip-up sweep whose per-site truncated SVD is taken
+by the randomized range finder (Halko, Martinsson, Tropp 2011, Alg. 4.4: a
+shared Philox test matrix, one subspace iteration, then an SVD of the projected
+matrix): the rank-R
+truncation that the library computes.  When R + oversampling covers the full
+column dimension the test matrix is the identity and the step is an exact
+truncated SVD.  ``zip_compress(exact=True)`` takes the plain SVD instead and is
+used to pin the range finder.
+
+Index conventions (logical order j = 0..W-1 along the sweep direction):
+  MPS site  m[a, Xc, Xp, a']   (Xc contracted with the MPO, Xp passed through)
+  MPO site  w[l, Xc, Y, r]
+  output    out[k, Y, Xp, k']
+Rows alternate direction (even rows left-to-right, odd rows right-to-left) so
+every zip starts at the orthogonality centre the previous one left behind.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import philox
+
+OVERSAMPLE = 8
+POWER_ITERS = 1
+
+
+# ---------------------------------------------------------------- small helpers
+def fix_phase(U: np.ndarray) -> np.ndarray:
+    """Deterministic column phases: make sum_i u_i / sqrt(i+1) real positive.
+
+    Falls back to the largest-magnitude entry when that sum vanishes.  Applied to
+    the columns of the compressed site tensor K (rows = (k, y, xp)), so the
+    convention does not depend on any internal basis.  Both the oracle and the
+    library use it so that the boundary MPS handed from row to row is the same
+    tensor, not just the same state.
+    """
+    U = U.copy()
+    w = 1.0 / np.sqrt(np.arange(U.shape[0]) + 1.0)
+    for j in range(U.shape[1]):
+        c = np.dot(w, U[:, j])
+        if abs(c) > 1e-8:
+            U[:, j] *= np.conj(c) / abs(c)
+        else:
+            i = int(np.argmax(np.abs(U[:, j])))
+            if abs(U[i, j]) > 0:
+                U[:, j] *= np.conj(U[i, j]) / abs(U[i, j])
+    return U
+
+
+def eigh_desc(A: np.ndarray):
+    lam, V = np.linalg.eigh(0.5 * (A + A.conj().T))
+    return lam[::-1], V[:, ::-1]
+
+
+def orth(Y: np.ndarray, gram_cut: float) -> np.ndarray:
+    """Orthonormal basis Q = Y V Lambda^{-1/2} of range(Y) from the Gram matrix Y^H Y.
+
+    Eigen-directions with lambda <= gram_cut * lambda_max are dropped.
+    """
+    lam, V = eigh_desc(Y.conj().T @ Y)
+    if lam[0] <= 0:
+        return np.zeros((Y.shape[0], 0), dtype=np.complex128)
+    keep = lam > gram_cut * lam[0]
+    return Y @ (V[:, keep] / np.sqrt(lam[keep]))
+
+
+def truncate(T: np.ndarray, R: int, omega, gram_cut: float = 1e-12, exact: bool = False,
+             power_iters: int = POWER_ITERS):
+    """Rank-R factorisation T ~ K C with K having orthonormal columns (the "QR + truncated SVD").
+
+    Randomized range finder with subspace iteration (Halko, Martinsson, Tropp
+    2011, Alg. 4.4): Y = T Omega, then ``power_iters`` times Y = T T^H orth(Y);
+    Omega = I (and no iteration) when k = R + p >= N, which makes the step an exact
+    truncated SVD.  Then Q = orth(Y), B = Q^H T, B B^H = U_B S^2 U_B^H, and
+    K = Q U_B[:, :R], C = K^H T.  Column phases of K follow ``fix_phase``.  K and C
+    depend only on range(Y) and T, not on the basis an implementation picks.
+    Returns K (M x Rk), C (Rk x N), Rk = min(R, M, N); unused columns are zero.
+    """
+    M, N = T.shape
+    Rk = min(R, M, N)
+    K = np.zeros((M, Rk), dtype=np.complex128)
+    if exact:
+        U, s, Vh = np.linalg.svd(T, full_matrices=False)
+        n = min(Rk, s.size)
+        K[:, :n] = fix_phase(U[:, :n])
+        return K, K.conj().T @ T
+    kk = min(R + OVERSAMPLE, M, N)
+    if kk == N:
+        Y = T
+    else:
+        Y = T @ omega(N, kk)
+        for _ in range(power_iters):
+            Y = T @ (T.conj().T @ orth(Y, gram_cut))
+    Q = orth(Y, gram_cut)
+    if Q.shape[1] == 0:
+        return K, np.zeros((Rk, N), dtype=np.complex128)
+    B = Q.conj().T @ T
+    mu, UB = eigh_desc(B @ B.conj().T)
+    n = min(Rk, UB.shape[1])
+    K[:, :n] = fix_phase(Q @ UB[:, :n])
+    return K, K.conj().T @ T
+
+
+def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=1e-12):
+    """Zip-up MPS-MPO compression to rank R along the given (logical) site order.
+
+    T_j[(k, y, xp), (a', r)] = sum C_{j-1}[k, a, l] m_j[a, xc, xp, a'] w_j[l, xc, y, r];
+    T_j = K_j C_j by ``truncate``; the last site keeps T / |T|.  Returns the output
+    MPS (sites out[k, y, xp, k']) and log|T_last| (the output's norm, since all
+    other sites are isometries).
+    """
+    W = len(mps)
+    C = np.ones((1, 1, 1), dtype=np.complex128)
+    out = []
+    log_scale = 0.0
+    for j in range(W):
+        m, w = mps[j], mpo[j]
+        X = np.tensordot(C, m, axes=([1], [0]))            # k, l, xc, xp, a'
+        T = np.tensordot(X, w, axes=([1, 2], [0, 1]))      # k, xp, a', y, r
+        T = np.transpose(T, (0, 3, 1, 2, 4))               # k, y, xp, a', r
+        k, y, xp, ap, r = T.shape
+        Tm = T.reshape(k * y * xp, ap * r)
+        if j == W - 1:
+            nrm = np.linalg.norm(Tm)
+            log_scale = float(np.log(nrm)) if nrm > 0 else -np.inf
+            out.append((Tm / nrm if nrm > 0 else Tm).reshape(k, y, xp, 1))
+            break
+        omega = lambda n, kk, _j=j: philox.test_matrix(seed, stage, row, _j, n, kk)
+        K, Cn = truncate(Tm, R, omega, gram_cut=gram_cut, exact=exact)
+        out.append(K.reshape(k, y, xp, K.shape[1]))
+        C = Cn.reshape(Cn.shape[0], ap, r)
+    return out, log_scale
+
+
+def mirror_mps(mps):
+    """Reverse the site order of an MPS (swap each site's bond axes)."""
+    return [np.swapaxes(x, 0, x.ndim - 1) for x in reversed(mps)]
+
+
+def row_tensors(tns, b, reverse):
+    """Row b's site tensors psi[s,u,l,d,r] in logical order (l<->r swapped if reversed)."""
+    row = [tns.T[b][c] for c in range(tns.W)]
+    if reverse:
+        row = [np.transpose(t, (0, 1, 4, 3, 2)) for t in reversed(row)]
+    return row
+
+
+def row_cells(tns, b, reverse):
+    cs = list(range(tns.W))
+    return list(reversed(cs)) if reverse else cs
+
+
+# ---------------------------------------------------------- norm environments
+def norm_envs(tns, R, seed, gram_cut=1e-12, exact=False):
+    """Bottom environments E[b] of <psi|psi> for b = 1..H (E[H] trivial).
+
+    E[b] is stored in column order with sites E[b][c][e, d, dbar, e'] on the
+    vertical bonds between rows b-1 and b.  Built once, independent of the
+    number of samples: absorb the ket row (zip left-to-right, compress to R),
+    then the bra row (zip right-to-left, compress to R).  Returns (E, log_norm)
+    where log_norm is log <psi|psi> from the last (b = 0) step.
+    """
+    H, W = tns.H, tns.W
+    E = {H: [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]}
+    log_norm = 0.0
+    for b in range(H - 1, -1, -1):
+        row = row_tensors(tns, b, reverse=False)
+        m = [x for x in E[b + 1]]                                   # e, d, dbar, e'
+        mpo = []
+        for t in row:                                                # ket: Xc = d, Y = (s, u)
+            s, u, l, d, r = t.shape
+            mpo.append(np.transpose(t, (2, 3, 0, 1, 4)).reshape(l, d, s * u, r))
+        Z, ls1 = zip_compress(m, mpo, R, seed, philox.STAGE_ENV_KET, b, exact=exact, gram_cut=gram_cut)
+        # Z_j: k, (s,u), dbar, k' -> bra input: Xc = (s, dbar), Xp = u
+        mz, mpo2 = [], []
+        for zj, t in zip(Z, row):
+            s, u, l, d, r = t.shape
+            k, _, db, kp = zj.shape
+            z5 = zj.reshape(k, s, u, db, kp)
+            mz.append(np.transpose(z5, (0, 1, 3, 2, 4)).reshape(k, s * db, u, kp))
+            mpo2.append(np.transpose(t.conj(), (2, 0, 3, 1, 4)).reshape(l, s * d, u, r))
+        mz, mpo2 = mirror_mps(mz), list(reversed([np.transpose(w, (3, 1, 2, 0)) for w in mpo2]))
+        Eb, ls2 = zip_compress(mz, mpo2, R, seed, philox.STAGE_ENV_BRA, b, exact=exact, gram_cut=gram_cut)
+        Eb = mirror_mps(Eb)                                          # back to column order
+        E[b] = [np.transpose(x, (0, 2, 1, 3)) for x in Eb]           # e, u(ket), ubar, e'
+        log_norm += ls1 + ls2
+    total = np.prod([x.reshape(()) for x in E[0]])
+    log_norm += float(np.log(abs(total))) if abs(total) > 0 else -np.inf
+    return E, log_norm
+
+
+# ------------------------------------------------------------------- sampler
+def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=1e-12, exact=False):
+    """One partition: absorb + compress, right environments, draw left to right.
+
+    m: MPS m[a, u, 1, a'] in this row's logical order; row: psi sites in logical
+    order; Eb: env sites [e, d, dbar, e'] in logical order.  Either ``uniforms``
+    (draw: x = 1 iff u >= q(0|prefix)) or ``forced`` bits (replay) is given.
+    Returns (bits, q0 per site, sum log q(x_j|prefix), m_next in logical order).
+    """
+    W = len(row)
+    mpo = []
+    for t in row:
+        s, u, l, d, r = t.shape
+        mpo.append(np.transpose(t, (2, 1, 0, 3, 4)).reshape(l, u, s * d, r))
+    Kp, _ = zip_compress(m, mpo, R, seed, philox.STAGE_SAMPLE, b, exact=exact, gram_cut=gram_cut)
+    K = [Kp[j].reshape(Kp[j].shape[0], row[j].shape[0], row[j].shape[3], Kp[j].shape[3]) for j in range(W)]
+    F = [None] * (W + 1)
+    F[W] = np.ones((1, 1, 1), dtype=np.complex128)
+    for j in range(W - 1, 0, -1):
+        # F_j[a, e, A] = sum K[a,s,d,b] E[e,d,f,g] conj K[A,s,f,B] F_{j+1}[b,g,B]
+        X = np.tensordot(K[j], F[j + 1], axes=([3], [0]))             # a, s, d, g, B
+        X = np.tensordot(X, Eb[j], axes=([2, 3], [1, 3]))             # a, s, B, e, f
+        Fj = np.tensordot(X, K[j].conj(), axes=([1, 2, 4], [1, 3, 2]))  # a, e, A
+        F[j] = Fj / np.linalg.norm(Fj)
+    L = np.ones((1, 1, 1), dtype=np.complex128)
+    bits = np.zeros(W, dtype=np.int64)
+    q0s = np.ones(W)
+    logq = 0.0
+    m_next = []
+    for j in range(W):
+        X = np.tensordot(L, K[j], axes=([0], [0]))                    # e, A, s, d, b
+        X = np.tensordot(X, Eb[j], axes=([0, 3], [0, 1]))             # A, s, b, f, g
+        G = np.einsum("Asbfg,AsfB->sbgB", X, K[j].conj())             # s, b, g, B
+        rho = np.real(np.tensordot(G, F[j + 1], axes=([1, 2, 3], [0, 1, 2])))
+        rho = np.maximum(rho, 0.0)
+        tot = float(rho.sum())
+        if row[j].shape[0] == 1:
+            x, q0 = 0, 1.0
+        else:
+            q0 = float(rho[0] / tot) if tot > 0 else 0.5
+            x = int(forced[j]) if forced is not None else int(uniforms[j] >= q0)
+            qx = q0 if x == 0 else 1.0 - q0
+            logq += float(np.log(qx)) if qx > 0 else -np.inf
+        bits[j] = x
+        q0s[j] = q0
+        L = G[x] / (tot if tot > 0 else 1.0)
+        m_next.append(K[j][:, x, :, :][:, :, None, :])                 # a, d, 1, a'
+    return bits, q0s, logq, m_next
+
+
+def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram_cut=1e-12, exact=False):
+    """Draw samples (or replay ``forced`` bitstrings); returns bits [n, n_qubits], log q, q0.
+
+    q0[n, qubit] is the conditional probability of 0 that the draw of that qubit used.
+    """
+    H, W = tns.H, tns.W
+    E = env if env is not None else norm_envs(tns, R, seed, gram_cut=gram_cut, exact=exact)[0]
+    n = n_samples if forced is None else forced.shape[0]
+    bits_out = np.zeros((n, tns.n), dtype=np.uint8)
+    q0_out = np.ones((n, tns.n))
+    logq = np.zeros(n)
+    for i in range(n):
+        sid = sample_offset + i
+        m = [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]
+        for b in range(H):
+            rev = (b % 2 == 1)
+            cells = row_cells(tns, b, rev)
+            row = row_tensors(tns, b, rev)
+            Eb = E[b + 1] if not rev else mirror_mps(E[b + 1])
+            qubits = [int(tns.cell_qubit[b, c]) for c in cells]
+            uni = fb = None
+            if forced is None:
+                uni = philox.draw_uniforms(seed, sid, np.array([max(q, 0) for q in qubits]))
+            else:
+                fb = [int(forced[i, q]) if q >= 0 else 0 for q in qubits]
+            xb, q0b, lq, m_next = sample_row(m, row, Eb, R, seed, b, uniforms=uni, forced=fb,
+                                             gram_cut=gram_cut, exact=exact)
+            logq[i] += lq
+            for j, q in enumerate(qubits):
+                if q >= 0:
+                    bits_out[i, q] = xb[j]
+                    q0_out[i, q] = q0b[j]
+            m = mirror_mps(m_next)
+    return bits_out, logq, q0_out
+
+
+def amplitude(tns, R, bits, seed, gram_cut=1e-12, exact=False):
+    """<x|psi> by single-layer boundary MPS over projected rows; returns (log|a|, phase)."""
+    H, W = tns.H, tns.W
+    m = [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]
+    log_abs = 0.0
+    out = None
+    for b in range(H):
+        rev = (b % 2 == 1)
+        cells = row_cells(tns, b, rev)
+        row = row_tensors(tns, b, rev)
+        mpo = []
+        for c, t in zip(cells, row):
+            q = int(tns.cell_qubit[b, c])
+            tp = t[int(bits[q]) if q >= 0 else 0]                       # u, l, d, r
+            mpo.append(np.transpose(tp, (1, 0, 2, 3)))                   # l, u, d, r
+        out, ls = zip_compress(m, mpo, R, seed, philox.STAGE_AMPLITUDE, b, exact=exact, gram_cut=gram_cut)
+        if not np.isfinite(ls):
+            return -np.inf, 0.0
+        log_abs += ls
+        m = mirror_mps(out)
+    z = np.prod([x.reshape(()) for x in out])
+    if abs(z) == 0:
+        return -np.inf, 0.0
+    return log_abs + float(np.log(abs(z))), float(np.angle(z))
