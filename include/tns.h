@@ -1,0 +1,172 @@
+/*
+ * tns.h -- C ABI of the GB300 boundary-MPS sampler for 2D tensor-network states.
+ *
+ * Method: Rudolph & Tindall, "Simulating and Sampling from Quantum Circuits with
+ * 2D Tensor Networks" (arXiv 2507.11424).  A processor-shaped tensor-network
+ * state (one tensor per qubit, bonds on the coupling graph; Methods) is built by
+ * belief-propagation-gauged simple update (Methods, Eqs. 1-2; Appendix Fig. 8)
+ * and sampled with the generalized boundary-MPS contraction (Appendix,
+ * "Sampling from a Tensor Network State", Fig. 7).
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return a tns_status; no exception crosses the ABI.  After
+ *     any error other than TNS_ERR_CUDA the state stays valid.  A thread-local
+ *     message is available from tns_last_error().
+ *   - Host arrays passed in are read during the call only (the caller keeps
+ *     ownership).  Device buffers passed in are caller-owned device memory on the
+ *     device that was current when the state was created; they are accessed on
+ *     the state's stream, and the call returns once that stream has finished
+ *     using them.
+ *   - Complex numbers are interleaved (re, im) float64 pairs.
+ *   - Qubit indices are the positions in the arrays given to tns_build_lattice;
+ *     bit x_q = 1 means |1>.
+ *   - A state is used by one host thread at a time.
+ */
+#ifndef TNS_H
+#define TNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNS_OK = 0,
+  TNS_ERR_ARG = 1,            /* invalid argument (sizes, indices, non-disjoint gates, ...) */
+  TNS_ERR_CUDA = 2,           /* a CUDA call failed; the state must be destroyed */
+  TNS_ERR_OOM = 3,            /* device allocation failed */
+  TNS_ERR_NOT_CONVERGED = 4,  /* BP stopped at max_iter; outputs hold the last iterate */
+  TNS_ERR_NUMERIC = 5,        /* NaN/Inf met, or a Jacobi sweep cap was reached */
+  TNS_ERR_STATE = 6           /* call not valid for this state (e.g. wrong file format) */
+} tns_status;
+
+typedef enum {
+  TNS_PREC_FP64 = 0,  /* every contraction and factorisation in FP64 */
+  TNS_PREC_MIXED = 1  /* sampler contractions in FP32 complex; Gram matrices, small
+                         eigenproblems (the truncation), probabilities and log q in FP64 */
+} tns_prec;
+
+typedef struct tns_state tns_state; /* opaque, library-owned */
+
+/*
+ * tns_build_lattice -- processor-shaped product state (Methods, first paragraph:
+ * one tensor per qubit, virtual bonds on the coupling graph).
+ *   n_sites   number of qubits (>= 1)
+ *   grid_rc   host int32 [n_sites][2]: (row, col) grid cell of each qubit; cells
+ *             must be distinct and non-negative.  The grid is transposed inside
+ *             the library when it has more columns than rows, so that the
+ *             boundary MPS runs along the shorter side.
+ *   n_edges, edges  host int32 [n_edges][2]: bonded qubit pairs; each pair must
+ *             occupy nearest-neighbour grid cells (planar grid embedding).
+ *   init_bits host uint8 [n_sites]: initial computational basis state.
+ *   chi_max   largest bond dimension any later call may request (sizes storage).
+ *   prec      default precision of tns_sample / tns_amplitude.
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream).
+ *   out       receives the new state (NULL on failure).
+ * Every bond starts at dimension 1 and every BP message at [1].
+ */
+tns_status tns_build_lattice(int32_t n_sites, const int32_t* grid_rc, int32_t n_edges, const int32_t* edges,
+                             const uint8_t* init_bits, int32_t chi_max, tns_prec prec, void* cuda_stream,
+                             tns_state** out);
+
+/*
+ * tns_apply_gate_layer -- apply one group of non-overlapping gates (Methods,
+ * edge colouring; Eq. HeisenbergProp) by BP-gauged simple update (Appendix,
+ * "Applying Gates", Fig. 8d): gauge each gate's two sites with the square roots
+ * of their incoming BP messages, reduce to R factors by QR, apply the gate,
+ * truncate the SVD to chi (Eq. 1), ungauge.  One-qubit gates are contracted
+ * exactly.  The state is not renormalised.
+ *   n_gates   number of gates; their qubits must be pairwise distinct
+ *   sites     host int32 [n_gates][2]; sites[g][1] = -1 marks a one-qubit gate;
+ *             two-qubit gates must act on a bonded pair
+ *   mats      host float64 [n_gates][16][2]: complex matrix, row-major,
+ *             U[2*o0 + o1][2*i0 + i1] with qubit sites[g][0] the high bit; a
+ *             one-qubit gate uses the first 4 entries as U[o][i]
+ *   chi       maximum bond dimension kept (1 <= chi <= chi_max)
+ *   svd_cutoff  singular values <= svd_cutoff * sigma_1 are dropped (e.g. 1e-14)
+ *   eps_out   host float64 [n_gates] or NULL: gate error eps_i (Eq. 1) as the
+ *             discarded fraction sum_{j>chi} s_j^2 / sum_j s_j^2; 0 for 1q gates
+ * After the call the BP messages on the gated bonds equal diag(S)/|S| and the
+ * others are stale until tns_bp_gauge runs.
+ */
+tns_status tns_apply_gate_layer(tns_state* s, int32_t n_gates, const int32_t* sites, const double* mats, int32_t chi,
+                                double svd_cutoff, double* eps_out);
+
+/*
+ * tns_bp_gauge -- run belief propagation on <psi|psi> (Methods; Appendix Fig. 8c):
+ * every message m_{v->v'} is replaced, in parallel, by psi_v psi_v^* contracted
+ * with all messages into v except the one from v', Hermitised and normalised to
+ * unit Frobenius norm, until max |m_new - m_old|_F < tol or max_iter sweeps.
+ *   iters_out, residual_out  host pointers or NULL.
+ * Returns TNS_ERR_NOT_CONVERGED (state still valid) when max_iter is reached.
+ */
+tns_status tns_bp_gauge(tns_state* s, int32_t max_iter, double tol, int32_t* iters_out, double* residual_out);
+
+/*
+ * tns_sample -- draw n_samples bitstrings with the boundary-MPS sampler (Appendix,
+ * Fig. 7d) at boundary rank chi_b (R_x = R_n = chi_b).  Rows of the (oriented)
+ * grid are the partitions.  The norm environments are contracted once from the
+ * bottom; each sample then absorbs row b into its boundary MPS, compresses it to
+ * chi_b (zip-up sweep; truncated SVD by a randomized range finder with one
+ * subspace iteration, exact when chi_b + 8 covers the column dimension), draws
+ * the row's qubits from their one-site conditionals, and projects.
+ *   seed      Philox4x32-10 key: qubit q of sample i uses counter
+ *             (i lo, i hi, q, 0); x_q = 1 iff u >= q(0 | prefix)
+ *   bits_dev  device uint8 [n_samples][n_sites] (caller-owned)
+ *   logq_dev  device float64 [n_samples]: log q(x), sum of log conditionals
+ *   cond_dev  device float64 [n_samples][n_sites] or NULL: q(x_q = 0 | prefix)
+ * Deterministic for a given (state, chi_b, seed, precision).
+ */
+tns_status tns_sample(tns_state* s, int32_t chi_b, int64_t n_samples, uint64_t seed, uint8_t* bits_dev,
+                      double* logq_dev, double* cond_dev);
+
+/*
+ * tns_sample_replay -- like tns_sample, but the bits are given (bits_dev is read,
+ * not written) and only the conditionals and log q along them are computed
+ * (forced-path replay; used to verify samples and to score bitstrings under q).
+ */
+tns_status tns_sample_replay(tns_state* s, int32_t chi_b, int64_t n, uint64_t seed, const uint8_t* bits_dev,
+                             double* logq_dev, double* cond_dev);
+
+/*
+ * tns_amplitude -- <x|psi> for n bitstrings by single-layer boundary MPS over the
+ * projected rows at rank chi_b (Methods, "p(x) = |<x|psi>|^2"; Appendix).
+ *   bits_dev     device uint8 [n][n_sites]
+ *   log_abs_dev  device float64 [n]: log |<x|psi>| (-inf for an exact zero)
+ *   phase_dev    device float64 [n]: arg <x|psi>
+ */
+tns_status tns_amplitude(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev, double* log_abs_dev,
+                         double* phase_dev);
+
+/* Sum over applied two-qubit gates of log(1 - eps_i): log of the fidelity
+ * estimate f of Eq. 2. */
+tns_status tns_log_fidelity(const tns_state* s, double* log_f);
+
+/* log <psi|psi> from the bottom norm environments at rank chi_b. */
+tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* log_norm);
+
+/* Select the precision of later tns_sample / tns_amplitude calls. */
+tns_status tns_set_precision(tns_state* s, tns_prec prec);
+
+/* Query: grid rows/cols after orientation, whether it was transposed, and the
+ * current maximum bond dimension. */
+tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int32_t* transposed, int32_t* chi_now);
+
+/* Save / load the state (site tensors, bond dimensions, messages, log f) to a
+ * little-endian binary file ("TNSF" format: header, then per grid cell its
+ * physical and bond dimensions and complex128 entries in [s][u][l][d][r] order,
+ * then the messages).  tns_load creates a new state on the given stream. */
+tns_status tns_save(const tns_state* s, const char* path);
+tns_status tns_load(const char* path, void* cuda_stream, tns_state** out);
+
+/* Number of library kernel launches issued since the state was created. */
+tns_status tns_launch_count(const tns_state* s, int64_t* launches);
+
+void tns_destroy(tns_state* s);
+const char* tns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNS_H */

@@ -1,0 +1,38 @@
+/*
+ * tns_testing.h -- test-only entry points of libtns.so that expose internal
+ * device primitives, so the test suite can check them against the CPU oracle
+ * one by one.  Not part of the sampling API; same conventions as tns.h
+ * (caller-owned device buffers, tns_status return codes).
+ */
+#ifndef TNS_TESTING_H
+#define TNS_TESTING_H
+
+#include <stdint.h>
+#include "tns.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32-10 (Salmon et al., SC'11) evaluated on the device.
+ *   ctr_key_dev  device uint32 [n][6]: counter words 0..3, key words 0..1
+ *   out_dev      device uint32 [n][4]: output words */
+tns_status tns_test_philox(int64_t n, const uint32_t* ctr_key_dev, uint32_t* out_dev, void* cuda_stream);
+
+/* Batched FP64 Hermitian eigendecomposition by parallel Jacobi.
+ *   A_dev    device complex128 [batch][n][n] (read only)
+ *   lam_dev  device float64 [batch][n], descending
+ *   V_dev    device complex128 [batch][n][n], column j = eigenvector j */
+tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
+                         void* cuda_stream);
+
+/* Batched FP64 thin SVD A = U diag(s) V^H (m >= n) by one-sided Jacobi.
+ *   A_dev  device complex128 [batch][m][n] (read only); s_dev float64 [batch][n];
+ *   U_dev  complex128 [batch][m][n]; V_dev complex128 [batch][n][n] */
+tns_status tns_test_svd(int32_t batch, int32_t m, int32_t n, const double* A_dev, double* s_dev, double* U_dev,
+                        double* V_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNS_TESTING_H */

@@ -166,14 +166,19 @@ def row_cells(tns, b, reverse):
 
 
 # ---------------------------------------------------------- norm environments
-def norm_envs(tns, R, seed, gram_cut=1e-12, exact=False):
+ENV_SEED = 0
+
+
+def norm_envs(tns, R, seed=ENV_SEED, gram_cut=1e-12, exact=False):
     """Bottom environments E[b] of <psi|psi> for b = 1..H (E[H] trivial).
 
     E[b] is stored in column order with sites E[b][c][e, d, dbar, e'] on the
     vertical bonds between rows b-1 and b.  Built once, independent of the
     number of samples: absorb the ket row (zip left-to-right, compress to R),
-    then the bra row (zip right-to-left, compress to R).  Returns (E, log_norm)
-    where log_norm is log <psi|psi> from the last (b = 0) step.
+    then the bra row (zip right-to-left, compress to R).  The range-finder test
+    matrices of the environments are keyed with ENV_SEED, independent of the
+    sampling seed.  Returns (E, log_norm) where log_norm is log <psi|psi> from the
+    last (b = 0) step.
     """
     H, W = tns.H, tns.W
     E = {H: [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]}
@@ -260,7 +265,7 @@ def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram
     q0[n, qubit] is the conditional probability of 0 that the draw of that qubit used.
     """
     H, W = tns.H, tns.W
-    E = env if env is not None else norm_envs(tns, R, seed, gram_cut=gram_cut, exact=exact)[0]
+    E = env if env is not None else norm_envs(tns, R, ENV_SEED, gram_cut=gram_cut, exact=exact)[0]
     n = n_samples if forced is None else forced.shape[0]
     bits_out = np.zeros((n, tns.n), dtype=np.uint8)
     q0_out = np.ones((n, tns.n))

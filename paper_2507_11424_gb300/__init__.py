@@ -1,0 +1,169 @@
+"""GB300-native boundary-MPS sampler for 2D tensor-network states (arXiv 2507.11424).
+
+Python view of the C ABI in ``include/tns.h``.  torch supplies device memory and
+the CUDA stream; every computation runs in the sm_103a kernels of libtns.so.
+
+    st = TNSState(lat.grid_rc, lat.edges, bits, chi_max=16)
+    for group in circuit:
+        st.apply_gate_layer(group, chi=16)
+        st.bp_gauge()
+    bits, logq = st.sample(chi_b=64, n=1024, seed=1)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+from ._native import PREC, TNSError, check, load  # noqa: F401
+
+__all__ = ["TNSState", "TNSError", "load", "pack_group"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def pack_group(group):
+    """Gate list [(q0, q1 or -1, U), ...] -> (sites int32 [g,2], mats float64 [g,16,2])."""
+    g = len(group)
+    sites = np.full((g, 2), -1, dtype=np.int32)
+    mats = np.zeros((g, 16, 2), dtype=np.float64)
+    for i, (a, b, U) in enumerate(group):
+        sites[i] = (a, b)
+        flat = np.asarray(U, dtype=np.complex128).reshape(-1)
+        mats[i, : flat.size, 0] = flat.real
+        mats[i, : flat.size, 1] = flat.imag
+    return sites, mats
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class TNSState:
+    """Owner of a library state (one processor-shaped TNS on the current GPU)."""
+
+    def __init__(self, grid_rc=None, edges=None, bits=None, chi_max: int = 16, prec: str = "mixed",
+                 stream=None, _handle=None):
+        self.lib = load()
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+            return
+        grid = np.ascontiguousarray(np.asarray(grid_rc, dtype=np.int32).reshape(-1, 2))
+        ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8).reshape(-1))
+        self.n = grid.shape[0]
+        check(self.lib.tns_build_lattice(grid.shape[0], _ptr(grid), ed.shape[0], _ptr(ed), _ptr(b), int(chi_max),
+                                         PREC[prec], _stream_handle(stream), C.byref(self._h)), "tns_build_lattice")
+
+    @classmethod
+    def load_file(cls, path: str, stream=None) -> "TNSState":
+        lib = load()
+        h = C.c_void_p()
+        check(lib.tns_load(path.encode(), _stream_handle(stream), C.byref(h)), "tns_load")
+        st = cls(_handle=h)
+        st.n = None
+        return st
+
+    def close(self):
+        if self._h:
+            self.lib.tns_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- circuit
+    def apply_gate_layer(self, group, chi: int, cutoff: float = 1e-14) -> np.ndarray:
+        sites, mats = group if isinstance(group, tuple) else pack_group(group)
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        mats = np.ascontiguousarray(mats, dtype=np.float64)
+        eps = np.zeros(sites.shape[0], dtype=np.float64)
+        check(self.lib.tns_apply_gate_layer(self._h, sites.shape[0], _ptr(sites), _ptr(mats), int(chi),
+                                            float(cutoff), _ptr(eps)), "tns_apply_gate_layer")
+        return eps
+
+    def bp_gauge(self, max_iter: int = 500, tol: float = 1e-12, strict: bool = False):
+        it = C.c_int32()
+        res = C.c_double()
+        allow = () if strict else (_native.TNS_ERR_NOT_CONVERGED,)
+        check(self.lib.tns_bp_gauge(self._h, int(max_iter), float(tol), C.byref(it), C.byref(res)),
+              "tns_bp_gauge", allow)
+        return it.value, res.value
+
+    def log_fidelity(self) -> float:
+        v = C.c_double()
+        check(self.lib.tns_log_fidelity(self._h, C.byref(v)), "tns_log_fidelity")
+        return v.value
+
+    def log_norm(self, chi_b: int) -> float:
+        v = C.c_double()
+        check(self.lib.tns_log_norm(self._h, int(chi_b), C.byref(v)), "tns_log_norm")
+        return v.value
+
+    def set_precision(self, prec: str):
+        check(self.lib.tns_set_precision(self._h, PREC[prec]), "tns_set_precision")
+
+    def query(self):
+        H, W, tr, chi = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        check(self.lib.tns_query(self._h, C.byref(H), C.byref(W), C.byref(tr), C.byref(chi)), "tns_query")
+        return dict(H=H.value, W=W.value, transposed=bool(tr.value), chi=chi.value)
+
+    def save(self, path: str):
+        check(self.lib.tns_save(self._h, path.encode()), "tns_save")
+
+    def launch_count(self) -> int:
+        v = C.c_int64()
+        check(self.lib.tns_launch_count(self._h, C.byref(v)), "tns_launch_count")
+        return v.value
+
+    # ---------------------------------------------------------------- sampling
+    def sample(self, chi_b: int, n: int, seed: int, n_sites: int | None = None, cond: bool = False, out=None):
+        """Draw n samples; returns torch CUDA tensors (bits uint8 [n, n_sites], logq f64 [n][, cond])."""
+        torch = _torch()
+        ns = n_sites or self.n
+        if out is None:
+            bits = torch.zeros((n, ns), dtype=torch.uint8, device="cuda")
+            logq = torch.zeros(n, dtype=torch.float64, device="cuda")
+            cnd = torch.zeros((n, ns), dtype=torch.float64, device="cuda") if cond else None
+        else:
+            bits, logq, cnd = out
+        check(self.lib.tns_sample(self._h, int(chi_b), int(n), C.c_uint64(int(seed) & (2**64 - 1)),
+                                  C.c_void_p(bits.data_ptr()), C.c_void_p(logq.data_ptr()),
+                                  C.c_void_p(cnd.data_ptr()) if cnd is not None else None), "tns_sample")
+        return (bits, logq, cnd) if cond else (bits, logq)
+
+    def sample_replay(self, chi_b: int, bits, seed: int = 0):
+        torch = _torch()
+        n, ns = bits.shape
+        logq = torch.zeros(n, dtype=torch.float64, device="cuda")
+        cnd = torch.zeros((n, ns), dtype=torch.float64, device="cuda")
+        check(self.lib.tns_sample_replay(self._h, int(chi_b), int(n), C.c_uint64(int(seed) & (2**64 - 1)),
+                                         C.c_void_p(bits.data_ptr()), C.c_void_p(logq.data_ptr()),
+                                         C.c_void_p(cnd.data_ptr())), "tns_sample_replay")
+        return logq, cnd
+
+    def amplitude(self, chi_b: int, bits):
+        torch = _torch()
+        n = bits.shape[0]
+        la = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ph = torch.zeros(n, dtype=torch.float64, device="cuda")
+        check(self.lib.tns_amplitude(self._h, int(chi_b), int(n), C.c_void_p(bits.data_ptr()),
+                                     C.c_void_p(la.data_ptr()), C.c_void_p(ph.data_ptr())), "tns_amplitude")
+        return la, ph

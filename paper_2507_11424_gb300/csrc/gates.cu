@@ -1,0 +1,465 @@
+// BP-gauged simple update (Methods, Eqs. 1-2; Appendix Fig. 8d) and belief
+// propagation (Appendix Fig. 8c) on the device, FP64 throughout.
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "linalg.cuh"
+#include "state.h"
+
+namespace tns {
+
+static const char LEGCH[5] = {'s', 'u', 'l', 'd', 'r'};
+
+static std::vector<long long> dims5(const int d[5]) { return {d[0], d[1], d[2], d[3], d[4]}; }
+
+// X = V diag(f(lam_c)) V^H with lam_c = max(lam, 1e-12 lam_max): f = sqrt (X) and 1/sqrt (Xi).
+__global__ void gauge_from_eig_kernel(const double* lam, const cd* V, int D, cd* X, cd* Xi) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= D * D) return;
+  int i = idx / D, j = idx % D;
+  double lmax = lam[0];
+  cd x = mk(0.0, 0.0), xi = mk(0.0, 0.0);
+  for (int k = 0; k < D; ++k) {
+    double l = lmax > 0.0 ? fmax(lam[k], 1e-12 * lmax) : 1.0;
+    double sq = sqrt(l);
+    cd p = cmul(V[i * D + k], cconj(V[j * D + k]));
+    x = cadd(x, cscale(p, sq));
+    xi = cadd(xi, cscale(p, 1.0 / sq));
+  }
+  X[idx] = x;
+  Xi[idx] = xi;
+}
+
+// W = V diag(lam^{-1/2}) keeping eigenvalues above cut * lam_max (others -> zero column).
+__global__ void gram_w_kernel(const double* lam, const cd* V, int n, double cut, cd* Wm) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int c = idx % n;
+  double l = lam[c], lmax = lam[0];
+  double f = (lmax > 0.0 && l > cut * lmax) ? 1.0 / sqrt(l) : 0.0;
+  Wm[idx] = cscale(V[idx], f);
+}
+
+// out[(row), b] = in[row, b] * sqrt(sigma_b) (optionally conjugated), b < k; in has ld cols.
+__global__ void scale_cols_kernel(const cd* in, int rows, int ld, int k, const double* sigma, int conj_in, cd* out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * k) return;
+  int r = idx / k, b = idx % k;
+  cd v = in[(long long)r * ld + b];
+  if (conj_in) v = cconj(v);
+  out[idx] = cscale(v, sqrt(sigma[b]));
+}
+
+__global__ void diag_msg_kernel(const double* sigma, int k, cd* m1, cd* m2) {
+  __shared__ double nrm;
+  if (threadIdx.x == 0) {
+    double s2 = 0;
+    for (int i = 0; i < k; ++i) s2 += sigma[i] * sigma[i];
+    nrm = sqrt(s2);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    int i = idx / k, j = idx % k;
+    cd v = mk(i == j && nrm > 0 ? sigma[i] / nrm : 0.0, 0.0);
+    m1[idx] = v;
+    m2[idx] = v;
+  }
+}
+
+struct MsgDesc {
+  cd* cur;
+  cd* nw;
+  int D;
+};
+
+// Hermitise and normalise every new message, write it over the current one and
+// record |m_new - m_old|_F per message.
+__global__ void bp_finish_kernel(const MsgDesc* md, double* resid) {
+  MsgDesc d = md[blockIdx.x];
+  __shared__ double red[256];
+  const int D = d.D;
+  double s2 = 0.0;
+  for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+    int i = idx / D, j = idx % D;
+    cd a = d.nw[i * D + j], b = cconj(d.nw[j * D + i]);
+    s2 += cabs2(cscale(cadd(a, b), 0.5));
+  }
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double nrm = sqrt(red[0]);
+  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  __syncthreads();
+  double df = 0.0;
+  for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+    int i = idx / D, j = idx % D;
+    cd a = d.nw[i * D + j], b = cconj(d.nw[j * D + i]);
+    cd h = cscale(cadd(a, b), 0.5 * inv);
+    cd o = d.cur[idx];
+    df += cabs2(csub(h, o));
+    d.cur[idx] = h;
+  }
+  red[threadIdx.x] = df;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) resid[blockIdx.x] = sqrt(red[0]);
+}
+
+static inline int blocks(long long n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// t'[.. J ..] = sum_j t[.. j ..] M[j, J] on axis `leg` of a [s][u][l][d][r] tensor.
+static cudaError_t apply_leg(const cd* src, const int d[5], int leg, const cd* M, cd* dst, cudaStream_t st) {
+  std::string lab = "suldr";
+  std::string out = lab;
+  out[leg] = (char)toupper(lab[leg]);
+  TView A = view((void*)src, lab, dims5(d));
+  TView B = view((void*)M, std::string() + lab[leg] + out[leg], {d[leg], d[leg]});
+  TView C = view(dst, out, dims5(d));
+  return contract(A, B, C, Prec::F64, st);
+}
+
+struct GateBufs {
+  cd *t1, *t2, *G, *V, *Wm, *QA, *QB, *RA, *RB, *P, *theta, *U, *VV, *Us, *gm, *X[10], *Xi[10];
+  double *lam, *sig;
+  int* status;
+};
+
+static tns_status gate_buffers(tns_state* s, GateBufs& b) {
+  const long long chi = s->chi_max;
+  long long tmax = 2;
+  for (auto& c : s->cell) tmax = std::max(tmax, c.cap);
+  const long long n = 2 * chi, m2 = 2 * n;  // R-factor rank and theta side
+  auto get = [&](const char* nm, size_t bytes, void** p) { return s->ws.get(nm, bytes, p); };
+  TNS_TRY_CUDA(get("g_t1", sizeof(cd) * tmax, (void**)&b.t1));
+  TNS_TRY_CUDA(get("g_t2", sizeof(cd) * tmax, (void**)&b.t2));
+  TNS_TRY_CUDA(get("g_G", sizeof(cd) * m2 * m2, (void**)&b.G));
+  TNS_TRY_CUDA(get("g_V", sizeof(cd) * m2 * m2, (void**)&b.V));
+  TNS_TRY_CUDA(get("g_W", sizeof(cd) * m2 * m2, (void**)&b.Wm));
+  TNS_TRY_CUDA(get("g_QA", sizeof(cd) * tmax, (void**)&b.QA));
+  TNS_TRY_CUDA(get("g_QB", sizeof(cd) * tmax, (void**)&b.QB));
+  TNS_TRY_CUDA(get("g_RA", sizeof(cd) * n * n, (void**)&b.RA));
+  TNS_TRY_CUDA(get("g_RB", sizeof(cd) * n * n, (void**)&b.RB));
+  TNS_TRY_CUDA(get("g_P", sizeof(cd) * m2 * m2, (void**)&b.P));
+  TNS_TRY_CUDA(get("g_theta", sizeof(cd) * m2 * m2, (void**)&b.theta));
+  TNS_TRY_CUDA(get("g_U", sizeof(cd) * m2 * m2, (void**)&b.U));
+  TNS_TRY_CUDA(get("g_VV", sizeof(cd) * m2 * m2, (void**)&b.VV));
+  TNS_TRY_CUDA(get("g_Us", sizeof(cd) * m2 * m2, (void**)&b.Us));
+  TNS_TRY_CUDA(get("g_gm", sizeof(cd) * 16 * 1024, (void**)&b.gm));
+  TNS_TRY_CUDA(get("g_lam", sizeof(double) * m2, (void**)&b.lam));
+  TNS_TRY_CUDA(get("g_sig", sizeof(double) * m2, (void**)&b.sig));
+  TNS_TRY_CUDA(get("g_status", sizeof(int) * 64, (void**)&b.status));
+  for (int i = 0; i < 10; ++i) {
+    char nm[32];
+    snprintf(nm, sizeof nm, "g_X%d", i);
+    TNS_TRY_CUDA(get(nm, sizeof(cd) * chi * chi, (void**)&b.X[i]));
+    snprintf(nm, sizeof nm, "g_Xi%d", i);
+    TNS_TRY_CUDA(get(nm, sizeof(cd) * chi * chi, (void**)&b.Xi[i]));
+  }
+  return TNS_OK;
+}
+
+// work buffer for Jacobi problems that do not fit in shared memory
+static tns_status jacobi_work(tns_state* s, int m, int n, int batch, cd** w) {
+  *w = nullptr;
+  if (jacobi_fits_smem(m, n)) return TNS_OK;
+  long long np = n + (n & 1);
+  TNS_TRY_CUDA(s->ws.get("jac_work", sizeof(cd) * batch * ((long long)m * np + np * np + 2 * np * np), (void**)w));
+  return TNS_OK;
+}
+
+// Gram-matrix orthonormalisation of the columns (s, j) of t viewed as
+// A[(others), (s, j)]: two passes of Q = A V Lambda^{-1/2}; R = Q^H A.
+static tns_status reduce_side(tns_state* s, GateBufs& b, const cd* t, const int d[5], int j, cd* Q, cd* R) {
+  cudaStream_t st = s->st;
+  const int n = d[0] * d[j];
+  std::string lab = "suldr";
+  std::string others;
+  std::vector<long long> odims;
+  for (int leg = 1; leg <= 4; ++leg)
+    if (leg != j) { others.push_back(lab[leg]); odims.push_back(d[leg]); }
+  std::string labA = lab, labB = lab;
+  labA[0] = 'S';
+  labA[j] = 'J';
+  // G[(S,J),(s,j)] = sum_others conj t t
+  TNS_TRY_CUDA(contract(view((void*)t, labA, dims5(d), true), view((void*)t, labB, dims5(d)),
+                        view(b.G, std::string("SJ") + 's' + lab[j], {d[0], d[j], d[0], d[j]}), Prec::F64, st));
+  cd* work = nullptr;
+  TNS_TRY(jacobi_work(s, n, n, 1, &work));
+  TNS_TRY_CUDA(eigh_batched(b.G, (long long)n * n, n, n, 1, b.lam, b.V, (long long)n * n, work, b.status, st));
+  gram_w_kernel<<<blocks((long long)n * n), 256, 0, st>>>(b.lam, b.V, n, 1e-30, b.Wm);
+  s->launches += 2;
+  // Q1[others, c] = sum_{s,j} t W1
+  std::vector<long long> qd = odims;
+  qd.push_back(n);
+  TNS_TRY_CUDA(contract(view((void*)t, lab, dims5(d)),
+                        view(b.Wm, std::string("s") + lab[j] + 'c', {d[0], d[j], n}),
+                        view(b.t2, others + 'c', qd), Prec::F64, st));
+  // second pass: G2 = Q1^H Q1, Q = Q1 W2
+  TNS_TRY_CUDA(contract(view(b.t2, others + 'C', qd, true), view(b.t2, others + 'c', qd), view(b.G, "Cc", {n, n}),
+                        Prec::F64, st));
+  TNS_TRY_CUDA(eigh_batched(b.G, (long long)n * n, n, n, 1, b.lam, b.V, (long long)n * n, work, b.status, st));
+  gram_w_kernel<<<blocks((long long)n * n), 256, 0, st>>>(b.lam, b.V, n, 1e-24, b.Wm);
+  s->launches += 2;
+  TNS_TRY_CUDA(contract(view(b.t2, others + 'c', qd), view(b.Wm, "cC", {n, n}), view(Q, others + 'C', qd),
+                        Prec::F64, st));
+  // R[c, (s, j)] = sum_others conj Q t
+  TNS_TRY_CUDA(contract(view(Q, others + 'c', qd, true), view((void*)t, lab, dims5(d)),
+                        view(R, std::string("cs") + lab[j], {n, d[0], d[j]}), Prec::F64, st));
+  return TNS_OK;
+}
+
+// Rebuild one side: new[others, o, b'] = sum_x Q[others, x] Us[x, o, b'] with Q of
+// n columns; then ungauge the external legs with the inverse square roots (the
+// last step writes the cell's storage).  c.dim already holds the new bond k.
+static tns_status rebuild_side(tns_state* s, GateBufs& b, Cell& c, int j, int n, const cd* Q, const cd* Us,
+                               const std::vector<int>& glegs, cd* const* Xi) {
+  cudaStream_t st = s->st;
+  const std::string lab = "suldr";
+  std::string others;
+  std::vector<long long> qd;
+  for (int leg = 1; leg <= 4; ++leg)
+    if (leg != j) { others.push_back(lab[leg]); qd.push_back(c.dim[leg]); }
+  qd.push_back(n);
+  const int k = c.dim[j];
+  cd* bufs[2] = {b.t1, b.t2};
+  cd* cur = glegs.empty() ? c.t : bufs[0];
+  TNS_TRY_CUDA(contract(view((void*)Q, others + 'x', qd),
+                        view((void*)Us, std::string("xs") + lab[j], {n, c.dim[0], k}),
+                        view(cur, lab, dims5(c.dim)), Prec::F64, st));
+  for (size_t i = 0; i < glegs.size(); ++i) {
+    cd* dst = (i + 1 == glegs.size()) ? c.t : bufs[(i + 1) & 1];
+    TNS_TRY_CUDA(apply_leg(cur, c.dim, glegs[i], Xi[i], dst, st));
+    cur = dst;
+  }
+  return TNS_OK;
+}
+
+// psi_tilde = psi x_l X_l over the listed legs; result in `out` (or psi itself if no legs).
+static tns_status gauge_side(tns_state* s, GateBufs& b, const Cell& c, const std::vector<int>& glegs, cd* const* X,
+                             cd* out, const cd** res) {
+  if (glegs.empty()) { *res = c.t; return TNS_OK; }
+  cd* bufs[2] = {b.t1, b.t2};
+  const cd* cur = c.t;
+  for (size_t i = 0; i < glegs.size(); ++i) {
+    cd* dst = (i + 1 == glegs.size()) ? out : bufs[i & 1];
+    TNS_TRY_CUDA(apply_leg(cur, c.dim, glegs[i], X[i], dst, s->st));
+    cur = dst;
+  }
+  *res = out;
+  return TNS_OK;
+}
+
+static tns_status gauge_mats(tns_state* s, GateBufs& b, int ci, const std::vector<int>& glegs, cd* const* X,
+                             cd* const* Xi) {
+  for (size_t i = 0; i < glegs.size(); ++i) {
+    int leg = glegs[i];
+    int D = s->cell[ci].dim[leg];
+    const cd* m = s->msg[ci * 5 + leg];
+    cd* work = nullptr;
+    TNS_TRY(jacobi_work(s, D, D, 1, &work));
+    TNS_TRY_CUDA(eigh_batched((cd*)m, (long long)D * D, D, D, 1, b.lam, b.V, (long long)D * D, work, b.status, s->st));
+    gauge_from_eig_kernel<<<blocks((long long)D * D), 256, 0, s->st>>>(b.lam, b.V, D, X[i], Xi[i]);
+    s->launches += 2;
+  }
+  return TNS_OK;
+}
+
+static int leg_between(const tns_state* s, int ca, int cb) {
+  int ra = ca / s->W, xa = ca % s->W, rb = cb / s->W, xb = cb % s->W;
+  if (rb == ra - 1 && xb == xa) return LEG_U;
+  if (rb == ra + 1 && xb == xa) return LEG_D;
+  if (rb == ra && xb == xa - 1) return LEG_L;
+  if (rb == ra && xb == xa + 1) return LEG_R;
+  return -1;
+}
+
+static tns_status apply_2q(tns_state* s, GateBufs& b, int q0, int q1, const cd* gmat, int chi, double cutoff,
+                           double* eps_out) {
+  cudaStream_t st = s->st;
+  const int ca = s->qcell[q0], cb = s->qcell[q1];
+  const int j = leg_between(s, ca, cb);
+  const int jb = opp_leg(j);
+  Cell& A = s->cell[ca];
+  Cell& B = s->cell[cb];
+  std::vector<int> ga, gb;
+  for (int leg = 1; leg <= 4; ++leg) {
+    if (leg != j && A.edge[leg]) ga.push_back(leg);
+    if (leg != jb && B.edge[leg]) gb.push_back(leg);
+  }
+  TNS_TRY(gauge_mats(s, b, ca, ga, b.X, b.Xi));
+  TNS_TRY(gauge_mats(s, b, cb, gb, b.X + 5, b.Xi + 5));
+  cd *gA = nullptr, *gB = nullptr;
+  TNS_TRY_CUDA(s->ws.get("g_gA", sizeof(cd) * A.cap, (void**)&gA));
+  TNS_TRY_CUDA(s->ws.get("g_gB", sizeof(cd) * B.cap, (void**)&gB));
+  const cd *tA = nullptr, *tB = nullptr;
+  TNS_TRY(gauge_side(s, b, A, ga, b.X, gA, &tA));
+  TNS_TRY(gauge_side(s, b, B, gb, b.X + 5, gB, &tB));
+  const int Dj = A.dim[j];
+  const int n = A.dim[0] * Dj;  // = B.dim[0] * Dj
+  TNS_TRY(reduce_side(s, b, tA, A.dim, j, b.QA, b.RA));
+  TNS_TRY(reduce_side(s, b, tB, B.dim, jb, b.QB, b.RB));
+  TNS_TRY_CUDA(contract(view(b.RA, "xsb", {n, 2, Dj}), view(b.RB, "ytb", {n, 2, Dj}), view(b.P, "xsyt", {n, 2, n, 2}),
+                        Prec::F64, st));
+  TNS_TRY_CUDA(contract(view((void*)gmat, "opst", {2, 2, 2, 2}), view(b.P, "xsyt", {n, 2, n, 2}),
+                        view(b.theta, "xoyp", {n, 2, n, 2}), Prec::F64, st));
+  const int m2 = 2 * n;
+  cd* work = nullptr;
+  TNS_TRY(jacobi_work(s, m2, m2, 1, &work));
+  TNS_TRY_CUDA(svd_batched(b.theta, (long long)m2 * m2, m2, m2, m2, 1, b.sig, b.U, (long long)m2 * m2, b.VV,
+                           (long long)m2 * m2, work, b.status, st));
+  s->launches += 1;
+  std::vector<double> sig(m2);
+  int status = 0;
+  TNS_TRY_CUDA(cudaMemcpyAsync(sig.data(), b.sig, sizeof(double) * m2, cudaMemcpyDeviceToHost, st));
+  TNS_TRY_CUDA(cudaMemcpyAsync(&status, b.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TNS_TRY_CUDA(cudaStreamSynchronize(st));
+  double tot = 0.0;
+  for (double x : sig) tot += x * x;
+  if (!std::isfinite(tot)) { set_error("non-finite singular values in gate on qubits %d,%d", q0, q1); return TNS_ERR_NUMERIC; }
+  int keep = 0;
+  for (double x : sig)
+    if (sig[0] > 0 && x > cutoff * sig[0]) ++keep;
+  int k = std::max(1, std::min(chi, keep));
+  double disc = 0.0;
+  for (int i = k; i < m2; ++i) disc += sig[i] * sig[i];
+  double eps = tot > 0.0 ? disc / tot : 0.0;
+  // side A
+  scale_cols_kernel<<<blocks((long long)m2 * k), 256, 0, st>>>(b.U, m2, m2, k, b.sig, 0, b.Us);
+  A.dim[j] = k;
+  TNS_TRY(rebuild_side(s, b, A, j, n, b.QA, b.Us, ga, b.Xi));
+  scale_cols_kernel<<<blocks((long long)m2 * k), 256, 0, st>>>(b.VV, m2, m2, k, b.sig, 1, b.Us);
+  B.dim[jb] = k;
+  TNS_TRY(rebuild_side(s, b, B, jb, n, b.QB, b.Us, gb, b.Xi + 5));
+  diag_msg_kernel<<<1, 256, 0, st>>>(b.sig, k, s->msg[ca * 5 + j], s->msg[cb * 5 + jb]);
+  s->launches += 3;
+  s->log_f += (eps < 1.0) ? std::log1p(-eps) : -INFINITY;
+  if (eps_out) *eps_out = eps;
+  if (status != 0) { set_error("SVD sweep cap reached in gate on qubits %d,%d", q0, q1); return TNS_ERR_NUMERIC; }
+  return TNS_OK;
+}
+
+tns_status apply_gate_layer(tns_state* s, int n_gates, const int32_t* sites, const double* mats, int chi,
+                            double cutoff, double* eps_out) {
+  std::vector<char> used(s->n, 0);
+  for (int g = 0; g < n_gates; ++g) {
+    int a = sites[2 * g], bq = sites[2 * g + 1];
+    if (a < 0 || a >= s->n || bq < -1 || bq >= s->n || a == bq) {
+      set_error("gate %d: invalid qubits (%d,%d)", g, a, bq);
+      return TNS_ERR_ARG;
+    }
+    if (used[a] || (bq >= 0 && used[bq])) {
+      set_error("gate %d overlaps another gate of the layer", g);
+      return TNS_ERR_ARG;
+    }
+    used[a] = 1;
+    if (bq >= 0) {
+      used[bq] = 1;
+      int j = leg_between(s, s->qcell[a], s->qcell[bq]);
+      if (j < 0 || !s->cell[s->qcell[a]].edge[j]) {
+        set_error("gate %d acts on qubits %d,%d that share no bond", g, a, bq);
+        return TNS_ERR_ARG;
+      }
+    }
+    for (int i = 0; i < 32; ++i)
+      if (!std::isfinite(mats[32 * g + i])) { set_error("gate %d has non-finite entries", g); return TNS_ERR_ARG; }
+  }
+  if (n_gates == 0) return TNS_OK;
+  GateBufs b;
+  TNS_TRY(gate_buffers(s, b));
+  cd* gm = nullptr;
+  TNS_TRY_CUDA(s->ws.get("g_gates", sizeof(cd) * 16 * n_gates, (void**)&gm));
+  TNS_TRY_CUDA(cudaMemcpyAsync(gm, mats, sizeof(cd) * 16 * n_gates, cudaMemcpyHostToDevice, s->st));
+  tns_status result = TNS_OK;
+  for (int g = 0; g < n_gates; ++g) {
+    int a = sites[2 * g], bq = sites[2 * g + 1];
+    double eps = 0.0;
+    if (bq < 0) {
+      Cell& c = s->cell[s->qcell[a]];
+      TNS_TRY_CUDA(contract(view(gm + 16 * g, "os", {2, 2}), view(c.t, "suldr", dims5(c.dim)),
+                            view(b.t1, "ouldr", dims5(c.dim)), Prec::F64, s->st));
+      TNS_TRY_CUDA(cudaMemcpyAsync(c.t, b.t1, sizeof(cd) * c.size(), cudaMemcpyDeviceToDevice, s->st));
+    } else {
+      tns_status r = apply_2q(s, b, a, bq, gm + 16 * g, chi, cutoff, &eps);
+      if (r == TNS_ERR_NUMERIC) result = r;
+      else if (r != TNS_OK) return r;
+    }
+    if (eps_out) eps_out[g] = eps;
+  }
+  s->version++;
+  TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
+  return result;
+}
+
+// ---------------------------------------------------------------- BP
+tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* resid) {
+  cudaStream_t st = s->st;
+  GateBufs b;
+  TNS_TRY(gate_buffers(s, b));
+  struct DirEdge { int ci, j, dst; };
+  std::vector<DirEdge> de;
+  std::vector<MsgDesc> md;
+  for (int ci = 0; ci < (int)s->cell.size(); ++ci)
+    for (int j = 1; j <= 4; ++j) {
+      if (!s->cell[ci].edge[j]) continue;
+      int r2, c2;
+      s->nbr(ci, j, r2, c2);
+      int dst = s->cidx(r2, c2) * 5 + opp_leg(j);
+      de.push_back({ci, j, dst});
+      md.push_back({s->msg[dst], s->msg_new[dst], s->cell[ci].dim[j]});
+    }
+  *iters = 0;
+  *resid = 0.0;
+  if (de.empty()) return TNS_OK;
+  MsgDesc* dmd = nullptr;
+  double* dres = nullptr;
+  TNS_TRY_CUDA(s->ws.get("bp_desc", sizeof(MsgDesc) * md.size(), (void**)&dmd));
+  TNS_TRY_CUDA(s->ws.get("bp_res", sizeof(double) * md.size(), (void**)&dres));
+  TNS_TRY_CUDA(cudaMemcpyAsync(dmd, md.data(), sizeof(MsgDesc) * md.size(), cudaMemcpyHostToDevice, st));
+  std::vector<double> hres(md.size());
+  const std::string lab = "suldr";
+  for (int it = 1; it <= max_iter; ++it) {
+    for (auto& e : de) {
+      const Cell& c = s->cell[e.ci];
+      cd* bufs[2] = {b.t1, b.t2};
+      const cd* cur = c.t;
+      int nb = 0;
+      for (int leg = 1; leg <= 4; ++leg) {
+        if (leg == e.j || !c.edge[leg]) continue;
+        cd* dst = bufs[nb & 1];
+        TNS_TRY_CUDA(apply_leg(cur, c.dim, leg, s->msg[e.ci * 5 + leg], dst, st));
+        cur = dst;
+        ++nb;
+      }
+      std::string la = lab, lb = lab;
+      la[e.j] = 'a';
+      lb[e.j] = 'b';
+      int D = c.dim[e.j];
+      TNS_TRY_CUDA(contract(view((void*)cur, la, dims5(c.dim)), view(c.t, lb, dims5(c.dim), true),
+                            view(s->msg_new[e.dst], "ab", {D, D}), Prec::F64, st));
+    }
+    bp_finish_kernel<<<(unsigned)md.size(), 256, 0, st>>>(dmd, dres);
+    s->launches++;
+    TNS_TRY_CUDA(cudaMemcpyAsync(hres.data(), dres, sizeof(double) * md.size(), cudaMemcpyDeviceToHost, st));
+    TNS_TRY_CUDA(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (double x : hres) {
+      if (!std::isfinite(x)) { set_error("non-finite BP message"); *iters = it; *resid = x; return TNS_ERR_NUMERIC; }
+      mx = std::max(mx, x);
+    }
+    *iters = it;
+    *resid = mx;
+    if (mx < tol) return TNS_OK;
+  }
+  set_error("BP not converged after %d iterations (residual %.3e)", max_iter, *resid);
+  return TNS_ERR_NOT_CONVERGED;
+}
+
+}  // namespace tns

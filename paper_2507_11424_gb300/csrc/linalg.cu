@@ -1,0 +1,304 @@
+// Batched FP64 Jacobi eigensolver and one-sided Jacobi SVD.  See linalg.cuh.
+//
+// Both use the round-robin ("chess tournament") ordering of index pairs, so the
+// n/2 rotations of a round act on disjoint indices and run in parallel.  Every
+// sweep loop is bounded (MAX_SWEEPS); a matrix that has not converged is
+// returned as is with status 1, never spun on.
+#include "linalg.cuh"
+
+namespace tns {
+
+static constexpr int JAC_THREADS = 256;
+static constexpr int MAX_SWEEPS = 40;
+static constexpr size_t SMEM_LIMIT = 200 * 1024;
+
+bool jacobi_fits_smem(int m, int n) {
+  size_t np = n + (n & 1);
+  size_t need = ((size_t)m * np + np * np) * sizeof(cd) + 1024;
+  return need <= SMEM_LIMIT;
+}
+
+__device__ inline void rr_pair(int r, int i, int np, int& p, int& q) {
+  int k = i, l = np - 1 - i;
+  p = (k == 0) ? 0 : 1 + (k - 1 + r) % (np - 1);
+  q = (l == 0) ? 0 : 1 + (l - 1 + r) % (np - 1);
+}
+
+// Rotation J = [[c, s], [-s conj(e), c conj(e)]] on (p, q) that zeroes the (p, q)
+// entry of J^H A J for the Hermitian 2x2 block [[app, apq], [conj(apq), aqq]]
+// (phase-reduce to a real symmetric block, then the symmetric Schur rotation).
+__device__ inline void herm_rot(double app, double aqq, cd apq, double& c, double& s, cd& e) {
+  double ab = sqrt(cabs2(apq));
+  if (!(ab > 1e-300)) {
+    c = 1.0; s = 0.0; e = mk(1.0, 0.0);
+    return;
+  }
+  e = mk(apq.x / ab, apq.y / ab);
+  double tau = (aqq - app) / (2.0 * ab);
+  double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+  c = 1.0 / hypot(1.0, t);
+  s = t * c;
+}
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(JAC_THREADS)
+eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long long sV, cd* work, int* status,
+            int use_smem) {
+  extern __shared__ double4 smraw4[];
+  __shared__ double cs_c[128], cs_s[128], cs_d[128];
+  __shared__ cd cs_e[128];
+  __shared__ double red[JAC_THREADS / 32];
+  __shared__ double floor_s;
+  __shared__ int nrot;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int np = n + (n & 1), half = np / 2;
+  cd* a = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * 2 * np * np;
+  cd* v = a + (long long)np * np;
+  const cd* src = Ain + (long long)b * sA;
+  double tot = 0.0;
+  for (int idx = tid; idx < np * np; idx += blockDim.x) {
+    int i = idx / np, j = idx % np;
+    cd x = (i < n && j < n) ? src[(long long)i * lda + j] : mk(0.0, 0.0);
+    if (i == j) x.y = 0.0;          // Hermitian: real diagonal
+    a[idx] = x;
+    tot += cabs2(x);
+    v[idx] = mk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  tot = warp_sum(tot);
+  if ((tid & 31) == 0) red[tid >> 5] = tot;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < JAC_THREADS / 32; ++w) t += red[w];
+    floor_s = 1e-17 * sqrt(t);      // absolute floor below which a pair counts as rotated
+  }
+  __syncthreads();
+  bool conv = (np <= 1);
+  for (int sweep = 0; sweep < MAX_SWEEPS && !conv; ++sweep) {
+    if (tid == 0) nrot = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int i = tid; i < half; i += blockDim.x) {
+        int p, q;
+        rr_pair(r, i, np, p, q);
+        double app = a[p * np + p].x, aqq = a[q * np + q].x;
+        cd apq = a[p * np + q];
+        double ab = sqrt(cabs2(apq));
+        double c = 1.0, s = 0.0, dl = 0.0;
+        cd e = mk(1.0, 0.0);
+        if (ab > floor_s && ab > 1e-15 * sqrt(fabs(app * aqq))) {
+          herm_rot(app, aqq, apq, c, s, e);
+          dl = (s / c) * ab;        // app' = app - t|apq|, aqq' = aqq + t|apq|
+          atomicAdd(&nrot, 1);
+        }
+        cs_c[i] = c; cs_s[i] = s; cs_e[i] = e; cs_d[i] = dl;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * np; idx += blockDim.x) {       // rows: J^H A
+        int i = idx / np, j = idx % np, p, q;
+        if (cs_s[i] == 0.0) continue;
+        rr_pair(r, i, np, p, q);
+        double c = cs_c[i], s = cs_s[i];
+        cd e = cs_e[i];
+        cd ap = a[p * np + j], aq = a[q * np + j];
+        cd eaq = cmul(e, aq);
+        a[p * np + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+        a[q * np + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * np; idx += blockDim.x) {       // columns: (J^H A) J and V J
+        int i = idx / np, j = idx % np, p, q;
+        if (cs_s[i] == 0.0) continue;
+        rr_pair(r, i, np, p, q);
+        double c = cs_c[i], s = cs_s[i];
+        cd ec = cconj(cs_e[i]);
+        cd ap = a[j * np + p], aq = a[j * np + q];
+        cd eaq = cmul(ec, aq);
+        a[j * np + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+        a[j * np + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+        cd vp = v[j * np + p], vq = v[j * np + q];
+        cd evq = cmul(ec, vq);
+        v[j * np + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
+        v[j * np + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
+      }
+      __syncthreads();
+      for (int i = tid; i < half; i += blockDim.x) {                   // exact 2x2 result
+        if (cs_s[i] == 0.0) continue;
+        int p, q;
+        rr_pair(r, i, np, p, q);
+        double app = a[p * np + p].x, aqq = a[q * np + q].x;
+        (void)app; (void)aqq;
+        a[p * np + q] = mk(0.0, 0.0);
+        a[q * np + p] = mk(0.0, 0.0);
+      }
+      __syncthreads();
+    }
+    conv = (nrot == 0);
+    __syncthreads();
+  }
+  if (tid == 0 && status) status[b] = conv ? 0 : 1;
+  for (int i = tid; i < n; i += blockDim.x) {
+    double li = a[i * np + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double lj = a[j * np + j].x;
+      if (lj > li || (lj == li && j < i)) ++rank;
+    }
+    lam[(long long)b * n + rank] = li;
+    cd* vo = Vout + (long long)b * sV;
+    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = v[row * np + i];
+  }
+}
+
+__global__ void __launch_bounds__(JAC_THREADS)
+svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout, long long sU, cd* Vout,
+           long long sV, cd* work, int* status, int use_smem) {
+  extern __shared__ double4 smraw4[];
+  __shared__ double wred[JAC_THREADS / 32];
+  __shared__ double sig[1024];
+  __shared__ int flag;
+  const int b = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nw = blockDim.x >> 5;
+  const int np = n + (n & 1), half = np / 2;
+  cd* a = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * ((long long)m * np + (long long)np * np);
+  cd* v = a + (long long)m * np;
+  const cd* src = Ain + (long long)b * sA;
+  for (long long idx = tid; idx < (long long)m * np; idx += blockDim.x) {
+    int i = (int)(idx / np), j = (int)(idx % np);
+    a[idx] = (j < n) ? src[(long long)i * lda + j] : mk(0.0, 0.0);
+  }
+  for (int idx = tid; idx < np * np; idx += blockDim.x) v[idx] = mk((idx / np == idx % np) ? 1.0 : 0.0, 0.0);
+  __shared__ double floor_s;
+  {
+    double t = 0.0;
+    for (long long idx = tid; idx < (long long)m * np; idx += blockDim.x) t += cabs2(a[idx]);
+    t = warp_sum(t);
+    if (lane == 0) wred[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double tt = 0.0;
+      for (int w = 0; w < nw; ++w) tt += wred[w];
+      floor_s = 1e-17 * tt;          // |gamma| scale is a squared column norm
+    }
+  }
+  __syncthreads();
+  const double tol = 1e-15 * sqrt((double)m);   // orthogonality threshold ~ sqrt(m) eps (LAPACK zgesvj style)
+  bool conv = (np <= 1);
+  for (int sweep = 0; sweep < MAX_SWEEPS && !conv; ++sweep) {
+    double wmax = 0.0;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int i = warp; i < half; i += nw) {
+        int p, q;
+        rr_pair(r, i, np, p, q);
+        double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
+        for (int row = lane; row < m; row += 32) {
+          cd x = a[(long long)row * np + p], y = a[(long long)row * np + q];
+          al += cabs2(x);
+          be += cabs2(y);
+          gx += x.x * y.x + x.y * y.y;     // conj(x) * y
+          gy += x.x * y.y - x.y * y.x;
+        }
+        al = warp_sum(al); be = warp_sum(be); gx = warp_sum(gx); gy = warp_sum(gy);
+        double gab = sqrt(gx * gx + gy * gy);
+        double den = sqrt(al * be);
+        if (gab > floor_s && den > 0.0 && gab > tol * den) {
+          wmax = fmax(wmax, gab / den);
+          cd ec = mk(gx / gab, -gy / gab);        // conj(e)
+          double tau = (be - al) / (2.0 * gab);
+          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+          double c = 1.0 / hypot(1.0, t), s = t * c;
+          for (int row = lane; row < m; row += 32) {
+            cd x = a[(long long)row * np + p], y = a[(long long)row * np + q];
+            cd ey = cmul(ec, y);
+            a[(long long)row * np + p] = mk(c * x.x - s * ey.x, c * x.y - s * ey.y);
+            a[(long long)row * np + q] = mk(s * x.x + c * ey.x, s * x.y + c * ey.y);
+          }
+          for (int row = lane; row < np; row += 32) {
+            cd x = v[row * np + p], y = v[row * np + q];
+            cd ey = cmul(ec, y);
+            v[row * np + p] = mk(c * x.x - s * ey.x, c * x.y - s * ey.y);
+            v[row * np + q] = mk(s * x.x + c * ey.x, s * x.y + c * ey.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    wmax = warp_max(wmax);
+    if (lane == 0) wred[warp] = wmax;
+    __syncthreads();
+    if (tid == 0) {
+      double mx = 0.0;
+      for (int w = 0; w < nw; ++w) mx = fmax(mx, wred[w]);
+      flag = (mx == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    conv = flag != 0;
+  }
+  if (tid == 0 && status) status[b] = conv ? 0 : 1;
+  for (int i = warp; i < n; i += nw) {
+    double s2 = 0.0;
+    for (int row = lane; row < m; row += 32) s2 += cabs2(a[(long long)row * np + i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[i] = sqrt(s2);
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    double si = sig[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double sj = sig[j];
+      if (sj > si || (sj == si && j < i)) ++rank;
+    }
+    sigma[(long long)b * n + rank] = si;
+    double inv = si > 0.0 ? 1.0 / si : 0.0;
+    cd* uo = Uout + (long long)b * sU;
+    for (int row = 0; row < m; ++row) uo[(long long)row * n + rank] = cscale(a[(long long)row * np + i], inv);
+    cd* vo = Vout + (long long)b * sV;
+    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = v[row * np + i];
+  }
+}
+
+cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV, cd* work,
+                         int* status, cudaStream_t st) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  if (n > 256) return cudaErrorInvalidValue;  // round parameters held in 128-entry tables
+  int np = n + (n & 1);
+  size_t bytes = (size_t)2 * np * np * sizeof(cd);
+  int use_smem = bytes <= SMEM_LIMIT;
+  if (!use_smem && !work) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    attr = true;
+  }
+  eigh_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, double* sigma, cd* U, long long sU,
+                        cd* V, long long sV, cd* work, int* status, cudaStream_t st) {
+  if (batch <= 0 || n <= 0 || m <= 0) return cudaSuccess;
+  if (n > 1024 || m < n) return cudaErrorInvalidValue;
+  int np = n + (n & 1);
+  size_t bytes = ((size_t)m * np + (size_t)np * np) * sizeof(cd);
+  int use_smem = bytes <= SMEM_LIMIT;
+  if (!use_smem && !work) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    attr = true;
+  }
+  svd_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, m, n, sigma, U, sU, V, sV, work, status,
+                                                              use_smem);
+  return cudaGetLastError();
+}
+
+}  // namespace tns

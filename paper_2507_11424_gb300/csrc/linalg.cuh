@@ -1,0 +1,28 @@
+// Batched small dense linear algebra in FP64 (Jacobi methods), sm_103a.
+#pragma once
+#include "common.cuh"
+
+namespace tns {
+
+// Hermitian eigendecomposition of a batch of n x n matrices by cyclic parallel
+// Jacobi (round-robin pair ordering, one thread block per matrix).
+//   A   : input, row-major, leading dim lda, batch stride sA (complex); destroyed
+//   lam : [batch][n] eigenvalues, descending
+//   V   : [batch] n x n row-major, column j = eigenvector j (batch stride sV)
+//   work: >= batch * 2 * np * np complex (np = n rounded up to even), used when the
+//         matrix does not fit in shared memory; may be null otherwise
+//   status: [batch] 0 = converged, 1 = sweep cap reached (result still returned)
+cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV,
+                         cd* work, int* status, cudaStream_t st);
+
+// Thin SVD A = U diag(sigma) V^H of a batch of m x n matrices with m >= n by
+// one-sided (Hestenes) Jacobi.  A (row-major, lda, batch stride sA) is destroyed.
+//   sigma: [batch][n] descending;  U: [batch] m x n row-major (zero columns where
+//   sigma = 0);  V: [batch] n x n row-major.  work as for eigh (m*np + np*np).
+cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, double* sigma, cd* U, long long sU,
+                        cd* V, long long sV, cd* work, int* status, cudaStream_t st);
+
+// Largest batch of n-sized problems that eigh/svd can run from shared memory.
+bool jacobi_fits_smem(int m, int n);
+
+}  // namespace tns

@@ -1,0 +1,953 @@
+// Generalized boundary-MPS sampler (Appendix "Sampling from a Tensor Network
+// State", Fig. 7) and single-layer amplitudes, batched over samples.
+//
+// Partitions are grid rows b = 0..H-1.  The norm environments E[b] (the paper's
+// M_{b -> b-1}) are contracted once from the bottom: absorb the ket row then the
+// bra row, each followed by a zip-up compression to rank R.  Each chunk of
+// samples then sweeps the rows: absorb row b into the sample's boundary MPS and
+// compress (zip-up; the truncated SVD of every site is taken by a randomized
+// range finder with one subspace iteration and a shared Philox test matrix),
+// contract the right environments F, and draw the row's qubits left to right
+// from their one-site conditionals, projecting as it goes.  Rows alternate
+// direction so every zip starts at the orthogonality centre the previous one
+// left behind.
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <vector>
+
+#include "linalg.cuh"
+#include "state.h"
+
+namespace tns {
+
+static inline int nblk(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 1 << 20); }
+
+// ------------------------------------------------------------------ kernels
+template <typename C> __global__ void convert_kernel(const cd* in, C* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = from_cd<C>(in[i]);
+}
+
+template <typename C> __global__ void fill_kernel(C* out, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = from_cd<C>(mk(v, 0.0));
+}
+
+// Range-finder test matrix Omega[i][j] (n x kk): Philox counter (i, j, row*4096+site,
+// 0x80000000 | stage), key = seed; Re from words 0,1 and Im from words 2,3, each 2u-1.
+template <typename C>
+__global__ void omega_kernel(C* out, int n, int kk, uint64_t seed, int stage, int row, int site) {
+  long long tot = (long long)n * kk;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    uint32_t i = (uint32_t)(idx / kk), j = (uint32_t)(idx % kk);
+    Philox4 w = philox4x32_10(i, j, (uint32_t)(row * 4096 + site), 0x80000000u | (uint32_t)stage,
+                              (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    double re = 2.0 * u53(w.v[0], w.v[1]) - 1.0, im = 2.0 * u53(w.v[2], w.v[3]) - 1.0;
+    out[idx] = from_cd<C>(mk(re, im));
+  }
+}
+
+// W = V diag(lam^{-1/2}) over eigenvalues > cut * lam_max, batched; converted to C.
+template <typename C>
+__global__ void gram_w_batched_kernel(const double* lam, const cd* V, int n, double cut, C* Wm, int batch) {
+  long long tot = (long long)batch * n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long b = idx / ((long long)n * n);
+    int c = (int)(idx % n);
+    double l = lam[b * n + c], lmax = lam[b * n];
+    double f = (lmax > 0.0 && l > cut * lmax) ? 1.0 / sqrt(l) : 0.0;
+    Wm[idx] = from_cd<C>(cscale(V[idx], f));
+  }
+}
+
+// UBt[b][i][r] = UB[b][i][r] for r < Rk (first Rk eigenvectors, descending).
+template <typename C> __global__ void take_cols_kernel(const cd* UB, int n, int Rk, C* out, int batch) {
+  long long tot = (long long)batch * n * Rk;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long b = idx / ((long long)n * Rk);
+    int rem = (int)(idx % ((long long)n * Rk));
+    int i = rem / Rk, r = rem % Rk;
+    out[idx] = from_cd<C>(UB[b * n * n + (long long)i * n + r]);
+  }
+}
+
+// Column phase convention: make sum_i K[i][col] / sqrt(i+1) real positive; when
+// that sum is below 1e-8, make the first largest-magnitude entry real positive.
+template <typename C> __global__ void phase_fix_kernel(C* K, int M, int Rk) {
+  const long long b = blockIdx.y;
+  const int col = blockIdx.x;
+  C* k = K + b * (long long)M * Rk + col;
+  __shared__ double sx[128], sy[128], sm[128];
+  __shared__ int si[128];
+  double cx = 0.0, cy = 0.0, best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    cd v = to_cd(k[(long long)i * Rk]);
+    double w = 1.0 / sqrt((double)i + 1.0);
+    cx += w * v.x;
+    cy += w * v.y;
+    double a = cabs2(v);
+    if (a > best) { best = a; bi = i; }
+  }
+  sx[threadIdx.x] = cx; sy[threadIdx.x] = cy; sm[threadIdx.x] = best; si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sx[threadIdx.x] += sx[threadIdx.x + o];
+      sy[threadIdx.x] += sy[threadIdx.x + o];
+      double m2 = sm[threadIdx.x + o];
+      int i2 = si[threadIdx.x + o];
+      if (m2 > sm[threadIdx.x] || (m2 == sm[threadIdx.x] && i2 < si[threadIdx.x])) { sm[threadIdx.x] = m2; si[threadIdx.x] = i2; }
+    }
+    __syncthreads();
+  }
+  __shared__ cd ph;
+  if (threadIdx.x == 0) {
+    double ax = sx[0], ay = sy[0], a = sqrt(ax * ax + ay * ay);
+    if (a > 1e-8) ph = mk(ax / a, -ay / a);
+    else if (sm[0] > 0.0 && si[0] < M) {
+      cd v = to_cd(k[(long long)si[0] * Rk]);
+      double av = sqrt(cabs2(v));
+      ph = mk(v.x / av, -v.y / av);
+    } else ph = mk(1.0, 0.0);
+  }
+  __syncthreads();
+  cd p = ph;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    cd v = to_cd(k[(long long)i * Rk]);
+    k[(long long)i * Rk] = from_cd<C>(cmul(v, p));
+  }
+}
+
+// K = T / |T| per batch entry; logscale[b] += log|T| (or -inf).
+template <typename C> __global__ void normalize_last_kernel(const C* T, long long M, C* K, double* logscale) {
+  const long long b = blockIdx.x;
+  __shared__ double red[256];
+  double s2 = 0.0;
+  for (long long i = threadIdx.x; i < M; i += blockDim.x) s2 += cabs2(to_cd(T[b * M + i]));
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double nrm = sqrt(red[0]);
+  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long long i = threadIdx.x; i < M; i += blockDim.x) K[b * M + i] = from_cd<C>(cscale(to_cd(T[b * M + i]), inv));
+  if (threadIdx.x == 0 && logscale) logscale[b] += nrm > 0.0 ? log(nrm) : -INFINITY;
+}
+
+// Scale each batch entry of F to unit Frobenius norm (conditionals are scale free).
+template <typename C> __global__ void normalize_kernel(C* F, long long n) {
+  const long long b = blockIdx.x;
+  __shared__ double red[256];
+  double s2 = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s2 += cabs2(to_cd(F[b * n + i]));
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double nrm = sqrt(red[0]);
+  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) F[b * n + i] = from_cd<C>(cscale(to_cd(F[b * n + i]), inv));
+}
+
+// One qubit of one sample per block: rho(s) = Re sum_e G[s][e] F[e]; q0 = rho0 / sum;
+// draw x = [u >= q0] (or read the forced bit); log q += log q(x); L_next = G[x] / sum;
+// m_next = K'[:, x, :, :].
+template <typename C>
+__global__ void marginal_kernel(const C* G, int P, long long nel, const C* F, long long fstride, const C* Kp,
+                                long long kstride, int ka, int Dd, int kb, C* Lnext, C* mnext, uint8_t* bits,
+                                const uint8_t* forced, int n_sites, int qubit, double* logq, double* cond,
+                                uint64_t seed, long long sample0) {
+  const long long sidx = blockIdx.x;
+  const C* g = G + sidx * P * nel;
+  const C* f = F + sidx * fstride;
+  __shared__ double r0[256], r1[256];
+  __shared__ int xs;
+  __shared__ double invs;
+  double a0 = 0.0, a1 = 0.0;
+  for (long long e = threadIdx.x; e < nel; e += blockDim.x) {
+    cd fv = to_cd(f[e]);
+    cd g0 = to_cd(g[e]);
+    a0 += g0.x * fv.x - g0.y * fv.y;
+    if (P > 1) {
+      cd g1 = to_cd(g[nel + e]);
+      a1 += g1.x * fv.x - g1.y * fv.y;
+    }
+  }
+  r0[threadIdx.x] = a0;
+  r1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { r0[threadIdx.x] += r0[threadIdx.x + o]; r1[threadIdx.x] += r1[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double p0 = fmax(r0[0], 0.0), p1 = (P > 1) ? fmax(r1[0], 0.0) : 0.0;
+    double tot = p0 + p1;
+    int x = 0;
+    if (P > 1) {
+      double q0 = tot > 0.0 ? p0 / tot : 0.5;
+      long long gs = sample0 + sidx;
+      if (forced) {
+        x = forced[gs * n_sites + qubit] ? 1 : 0;
+      } else {
+        Philox4 w = philox4x32_10((uint32_t)((uint64_t)gs & 0xffffffffu), (uint32_t)((uint64_t)gs >> 32),
+                                  (uint32_t)qubit, 0u, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+        double u = u53(w.v[0], w.v[1]);
+        x = (u >= q0) ? 1 : 0;
+        bits[gs * n_sites + qubit] = (uint8_t)x;
+      }
+      double qx = x ? 1.0 - q0 : q0;
+      logq[gs] += qx > 0.0 ? log(qx) : -INFINITY;
+      if (cond) cond[gs * n_sites + qubit] = q0;
+    }
+    xs = x;
+    invs = tot > 0.0 ? 1.0 / tot : 1.0;
+  }
+  __syncthreads();
+  const int x = xs;
+  const double inv = invs;
+  for (long long e = threadIdx.x; e < nel; e += blockDim.x)
+    Lnext[sidx * nel + e] = from_cd<C>(cscale(to_cd(g[(long long)x * nel + e]), inv));
+  const C* kp = Kp + sidx * kstride;
+  long long nm = (long long)ka * Dd * kb;
+  for (long long e = threadIdx.x; e < nm; e += blockDim.x) {
+    long long a = e / ((long long)Dd * kb), rem = e % ((long long)Dd * kb);
+    mnext[sidx * nm + e] = kp[((a * P + x) * Dd) * kb + rem];
+  }
+}
+
+// Amplitude of the final (all dimension 1) boundary MPS: product of W scalars.
+template <typename C>
+__global__ void amp_final_kernel(const C* const* sites, int W, long long S, double* log_abs, double* phase) {
+  long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= S) return;
+  cd z = mk(1.0, 0.0);
+  for (int j = 0; j < W; ++j) z = cmul(z, to_cd(sites[j][b]));
+  double a = sqrt(cabs2(z));
+  if (a > 0.0 && isfinite(log_abs[b])) {
+    log_abs[b] += log(a);
+    phase[b] = atan2(z.y, z.x);
+  } else {
+    log_abs[b] = -INFINITY;
+    phase[b] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct Ctx {
+  tns_state* s;
+  cudaStream_t st;
+  bool f64;
+  Prec gp, gram;
+  size_t esz;
+  uint64_t seed;
+  int R;
+};
+
+template <typename F> static void dispatch(bool f64, F&& f) {
+  if (f64) f((cd*)nullptr);
+  else f((cf*)nullptr);
+}
+
+static tns_status ensure_work_cells(tns_state* s, bool f64) {
+  int want = f64 ? 0 : 1;
+  if (s->work_prec == want && s->work_version == s->version && !s->work_cells.empty()) return TNS_OK;
+  if (s->work_cells.empty()) s->work_cells.assign(s->cell.size(), nullptr);
+  for (size_t ci = 0; ci < s->cell.size(); ++ci) {
+    Cell& c = s->cell[ci];
+    if (f64) {
+      s->work_cells[ci] = nullptr;  // FP64 reads the master copy
+      continue;
+    }
+    if (!s->work_cells[ci]) TNS_TRY_CUDA(cudaMalloc(&s->work_cells[ci], sizeof(cf) * c.cap));
+    convert_kernel<cf><<<nblk(c.size()), 256, 0, s->st>>>(c.t, (cf*)s->work_cells[ci], c.size());
+    s->launches++;
+  }
+  s->work_prec = want;
+  s->work_version = s->version;
+  return TNS_OK;
+}
+
+static void* cell_ptr(tns_state* s, int ci, bool f64) { return f64 ? (void*)s->cell[ci].t : s->work_cells[ci]; }
+
+// Row b, logical site j (rev: right to left); labels for (s, u, logical-left, d, logical-right).
+static TView cell_view(tns_state* s, bool f64, int b, int j, bool rev, char ls, char lu, char la, char ld, char lb,
+                       bool conj = false) {
+  int c = rev ? s->W - 1 - j : j;
+  int ci = s->cidx(b, c);
+  const Cell& cc = s->cell[ci];
+  std::string lab = {ls, lu, rev ? lb : la, ld, rev ? la : lb};
+  return view(cell_ptr(s, ci, f64), lab, {cc.dim[0], cc.dim[1], cc.dim[2], cc.dim[3], cc.dim[4]}, conj);
+}
+
+// Site of a stored MPS seen at logical site j of a row swept in direction rev,
+// labels (logical-left, phys..., logical-right); optional leading sample axis.
+static TView mps_view(const StoredMPS& m, int W, int j, bool rev, char la, const std::string& phys, char lb,
+                      long long S, long long sstride, bool conj = false) {
+  int c = rev ? W - 1 - j : j;
+  int i = m.reversed ? W - 1 - c : c;
+  bool same = (m.reversed == rev);
+  std::string lab;
+  std::vector<long long> dims;
+  lab.push_back(same ? la : lb);
+  dims.push_back(m.bond[i]);
+  for (size_t k = 0; k < phys.size(); ++k) { lab.push_back(phys[k]); dims.push_back(m.phys[i][k]); }
+  lab.push_back(same ? lb : la);
+  dims.push_back(m.bond[i + 1]);
+  TView v = view(m.site[i], lab, dims, conj);
+  if (S > 0) {
+    v.labels.insert(v.labels.begin(), 'S');
+    v.dim.insert(v.dim.begin(), S);
+    v.stride.insert(v.stride.begin(), sstride);
+  }
+  return v;
+}
+
+// Elements of logical site j (row direction rev) of a stored MPS.
+static long long mps_site_size(const StoredMPS& m, int W, int j, bool rev) {
+  int c = rev ? W - 1 - j : j;
+  int i = m.reversed ? W - 1 - c : c;
+  long long n = m.bond[i] * m.bond[i + 1];
+  for (auto d : m.phys[i]) n *= d;
+  return n;
+}
+
+static long long vdim(const TView& v, char l) {
+  for (size_t i = 0; i < v.labels.size(); ++i)
+    if (v.labels[i] == l) return v.dim[i];
+  return -1;
+}
+
+static long long vsize_nos(const TView& v) {
+  long long n = 1;
+  for (size_t i = 0; i < v.labels.size(); ++i)
+    if (v.labels[i] != 'S') n *= v.dim[i];
+  return n;
+}
+
+struct ZipSpec {
+  long long S;                                  // batch of the zip (1 = shared)
+  std::function<TView(int)> mview;              // labels S a Pm b
+  std::function<TView(int)> wview;              // labels l Pw r (+ S)
+  std::string out_phys;                         // labels of the output physical legs
+  int stage, row;
+  bool rev;
+  StoredMPS* out;                               // site buffers preassigned, S*cap each
+  double* logscale;                             // device [S], += log |T_last| (may be null)
+};
+
+// Workspace request helper with a per-sample capacity.
+static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
+  TNS_TRY_CUDA(s->ws.get(nm, bytes, p));
+  return TNS_OK;
+}
+
+// Orthonormalising map W (kk x kk) with Y W orthonormal, from the Gram matrix (FP64 eigh).
+static tns_status orth_w(Ctx& cx, void* Y, long long S, long long M, int kk, void* Wout) {
+  tns_state* s = cx.s;
+  cd *G, *V;
+  double* lam;
+  int* status;
+  TNS_TRY(wsget(s, "z_G", sizeof(cd) * S * kk * kk, (void**)&G));
+  TNS_TRY(wsget(s, "z_V", sizeof(cd) * S * kk * kk, (void**)&V));
+  TNS_TRY(wsget(s, "z_lam", sizeof(double) * S * kk, (void**)&lam));
+  TNS_TRY(wsget(s, "z_status", sizeof(int) * S, (void**)&status));
+  TNS_TRY_CUDA(contract(view(Y, "Smc", {S, M, kk}, true), view(Y, "Sme", {S, M, kk}), view(G, "Sce", {S, kk, kk}),
+                        cx.gram, cx.st));
+  cd* work = nullptr;
+  if (!jacobi_fits_smem(kk, kk)) {
+    long long np = kk + (kk & 1);
+    TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
+  }
+  TNS_TRY_CUDA(eigh_batched(G, (long long)kk * kk, kk, kk, (int)S, lam, V, (long long)kk * kk, work, status, cx.st));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    gram_w_batched_kernel<C><<<nblk(S * kk * kk), 256, 0, cx.st>>>(lam, V, kk, 1e-12, (C*)Wout, (int)S);
+  });
+  s->launches += 2;
+  return TNS_OK;
+}
+
+// Rank-R factorisation T = K C of each batch entry (T: S x M x N).  K has
+// orthonormal columns with the phase convention; C = K^H T.
+static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long N, int stage, int row, int site,
+                           void* Kout, void* Cout, int* Rk_out) {
+  tns_state* s = cx.s;
+  const int kk = (int)std::min<long long>(std::min<long long>(cx.R + 8, M), N);
+  const int Rk = (int)std::min<long long>(std::min<long long>(cx.R, M), N);
+  *Rk_out = Rk;
+  void *Y, *Q, *Z, *B, *Wm, *UBt, *om;
+  TNS_TRY(wsget(s, "z_Y", cx.esz * S * M * kk, &Y));
+  TNS_TRY(wsget(s, "z_Q", cx.esz * S * M * kk, &Q));
+  TNS_TRY(wsget(s, "z_Z", cx.esz * S * N * kk, &Z));
+  TNS_TRY(wsget(s, "z_B", cx.esz * S * N * kk, &B));
+  TNS_TRY(wsget(s, "z_W", cx.esz * S * kk * kk, &Wm));
+  TNS_TRY(wsget(s, "z_UBt", cx.esz * S * kk * kk, &UBt));
+  void* Ymat = Y;
+  if (kk == N) {
+    Ymat = T;  // test matrix = identity: the range of T is captured exactly
+  } else {
+    TNS_TRY(wsget(s, "z_om", cx.esz * N * kk, &om));
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      omega_kernel<C><<<nblk(N * kk), 256, 0, cx.st>>>((C*)om, (int)N, kk, cx.seed, stage, row, site);
+    });
+    s->launches++;
+    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}), cx.gp, cx.st));
+    // one subspace iteration: Y <- T T^H orth(Y)
+    TNS_TRY(orth_w(cx, Y, S, M, kk, Wm));
+    TNS_TRY_CUDA(contract(view(Y, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}), view(Q, "Sme", {S, M, kk}), cx.gp,
+                          cx.st));
+    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}, true), view(Q, "Sme", {S, M, kk}), view(Z, "Sne", {S, N, kk}),
+                          cx.gp, cx.st));
+    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}), view(Z, "Sne", {S, N, kk}), view(Y, "Sme", {S, M, kk}), cx.gp,
+                          cx.st));
+  }
+  TNS_TRY(orth_w(cx, Ymat, S, M, kk, Wm));
+  TNS_TRY_CUDA(contract(view(Ymat, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}), view(Q, "Sme", {S, M, kk}),
+                        cx.gp, cx.st));
+  TNS_TRY_CUDA(contract(view(Q, "Sme", {S, M, kk}, true), view(T, "Smn", {S, M, N}), view(B, "Sen", {S, kk, N}),
+                        cx.gp, cx.st));
+  cd *Hm, *V;
+  double* mu;
+  int* status;
+  TNS_TRY(wsget(s, "z_H", sizeof(cd) * S * kk * kk, (void**)&Hm));
+  TNS_TRY(wsget(s, "z_V2", sizeof(cd) * S * kk * kk, (void**)&V));
+  TNS_TRY(wsget(s, "z_mu", sizeof(double) * S * kk, (void**)&mu));
+  TNS_TRY(wsget(s, "z_status2", sizeof(int) * S, (void**)&status));
+  TNS_TRY_CUDA(contract(view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true), view(Hm, "Sef", {S, kk, kk}),
+                        cx.gram, cx.st));
+  cd* work = nullptr;
+  if (!jacobi_fits_smem(kk, kk)) {
+    long long np = kk + (kk & 1);
+    TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
+  }
+  TNS_TRY_CUDA(eigh_batched(Hm, (long long)kk * kk, kk, kk, (int)S, mu, V, (long long)kk * kk, work, status, cx.st));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    take_cols_kernel<C><<<nblk(S * kk * Rk), 256, 0, cx.st>>>(V, kk, Rk, (C*)UBt, (int)S);
+  });
+  TNS_TRY_CUDA(contract(view(Q, "Sme", {S, M, kk}), view(UBt, "Ser", {S, kk, Rk}), view(Kout, "Smr", {S, M, Rk}),
+                        cx.gp, cx.st));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    phase_fix_kernel<C><<<dim3(Rk, (unsigned)S), 128, 0, cx.st>>>((C*)Kout, (int)M, Rk);
+  });
+  TNS_TRY_CUDA(contract(view(Kout, "Smr", {S, M, Rk}, true), view(T, "Smn", {S, M, N}), view(Cout, "Srn", {S, Rk, N}),
+                        cx.gp, cx.st));
+  s->launches += 3;
+  return TNS_OK;
+}
+
+// Zip-up compression of (MPS . MPO) to rank R along the spec's logical order.
+static tns_status zip(Ctx& cx, ZipSpec& zs) {
+  tns_state* s = cx.s;
+  const int W = s->W;
+  const long long S = zs.S;
+  StoredMPS& out = *zs.out;
+  out.reversed = zs.rev;
+  out.bond.assign(W + 1, 1);
+  out.phys.assign(W, {});
+  void *Cp, *Cn, *X, *T;
+  long long kprev = 1;
+  // C_{-1} = 1
+  long long chi = 1;
+  for (auto& c : s->cell)
+    for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, c.dim[leg]);
+  const long long Ccap = (long long)cx.R * cx.R * chi;   // C[k][a][l]: k, a <= R, l <= chi
+  TNS_TRY(wsget(s, "zip_C0", cx.esz * S * Ccap, &Cp));
+  TNS_TRY(wsget(s, "zip_C1", cx.esz * S * Ccap, &Cn));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    fill_kernel<C><<<nblk(S), 256, 0, cx.st>>>((C*)Cp, S, 1.0);
+  });
+  s->launches++;
+  long long a_prev = 1, l_prev = 1;
+  for (int j = 0; j < W; ++j) {
+    TView mv = zs.mview(j);
+    TView wv = zs.wview(j);
+    // labels of m: [S] a Pm b ; w: l Pw r [S]
+    std::string Pm, Pw;
+    for (char c : mv.labels)
+      if (c != 'S' && c != 'a' && c != 'b') Pm.push_back(c);
+    for (char c : wv.labels)
+      if (c != 'S' && c != 'l' && c != 'r') Pw.push_back(c);
+    const long long a = vdim(mv, 'a'), bdm = vdim(mv, 'b'), l = vdim(wv, 'l'), r = vdim(wv, 'r');
+    if (a != a_prev || l != l_prev) {
+      set_error("zip: bond mismatch at site %d (a %lld/%lld, l %lld/%lld)", j, a, a_prev, l, l_prev);
+      return TNS_ERR_STATE;
+    }
+    // X[S][k][l][Pm][b] = sum_a C[S][k][a][l] m[S][a][Pm][b]
+    std::vector<long long> xd = {S, kprev, l};
+    std::string xl = "Skl";
+    long long xsz = kprev * l;
+    for (char c : Pm) { xl.push_back(c); long long d = vdim(mv, c); xd.push_back(d); xsz *= d; }
+    xl.push_back('b');
+    xd.push_back(bdm);
+    xsz *= bdm;
+    TNS_TRY(wsget(s, "zip_X", cx.esz * S * xsz, &X));
+    TNS_TRY_CUDA(contract(view(Cp, "Skal", {S, kprev, a, l}), mv, view(X, xl, xd), cx.gp, cx.st));
+    // T[S][k][out][b][r] = sum_{l, Pc} X w
+    std::vector<long long> td = {S, kprev};
+    std::string tl = "Sk";
+    long long Mrow = kprev;
+    std::vector<long long> pdims;
+    for (char c : zs.out_phys) {
+      long long d = vdim(mv, c);
+      if (d < 0) d = vdim(wv, c);
+      tl.push_back(c);
+      td.push_back(d);
+      pdims.push_back(d);
+      Mrow *= d;
+    }
+    tl += "br";
+    td.push_back(bdm);
+    td.push_back(r);
+    const long long Ncol = bdm * r;
+    TNS_TRY(wsget(s, "zip_T", cx.esz * S * Mrow * Ncol, &T));
+    TNS_TRY_CUDA(contract(view(X, xl, xd), wv, view(T, tl, td), cx.gp, cx.st));
+    out.phys[j] = pdims;
+    if (j == W - 1) {
+      if (Ncol != 1) { set_error("zip: open right bond at the last site"); return TNS_ERR_STATE; }
+      dispatch(cx.f64, [&](auto* tp) {
+        using C = std::remove_pointer_t<decltype(tp)>;
+        normalize_last_kernel<C><<<(unsigned)S, 256, 0, cx.st>>>((C*)T, Mrow, (C*)out.site[j], zs.logscale);
+      });
+      s->launches++;
+      out.bond[j] = kprev;
+      out.bond[j + 1] = 1;
+      break;
+    }
+    int Rk = 0;
+    TNS_TRY(truncate(cx, T, S, Mrow, Ncol, zs.stage, zs.row, j, out.site[j], Cn, &Rk));
+    out.bond[j] = kprev;
+    out.bond[j + 1] = Rk;
+    std::swap(Cp, Cn);
+    kprev = Rk;
+    a_prev = bdm;
+    l_prev = r;
+  }
+  return TNS_OK;
+}
+
+static void free_mps(StoredMPS& m) {
+  for (auto p : m.site)
+    if (p) cudaFree(p);
+  m.site.clear();
+}
+
+// Bottom norm environments E[b], b = H..0 (E[0] gives <psi|psi>), at rank R.
+static tns_status build_envs(Ctx& cx_in) {
+  // environment test matrices use key 0, independent of the sampling seed
+  Ctx cx = cx_in;
+  cx.seed = 0;
+  tns_state* s = cx.s;
+  EnvCache& ec = s->env;
+  const int prec = cx.f64 ? 0 : 1;
+  if (ec.valid && ec.chi_b == cx.R && ec.prec == prec && ec.version == s->version) return TNS_OK;
+  for (auto& E : ec.E) free_mps(E);
+  ec.E.assign(s->H + 1, StoredMPS());
+  ec.valid = false;
+  const int H = s->H, W = s->W;
+  // E[H]: trivial
+  StoredMPS& EH = ec.E[H];
+  EH.reversed = true;
+  EH.bond.assign(W + 1, 1);
+  EH.phys.assign(W, {1, 1});
+  EH.site.assign(W, nullptr);
+  for (int c = 0; c < W; ++c) {
+    TNS_TRY_CUDA(cudaMalloc(&EH.site[c], cx.esz));
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      fill_kernel<C><<<1, 32, 0, cx.st>>>((C*)EH.site[c], 1, 1.0);
+    });
+  }
+  double* dlog;
+  TNS_TRY(wsget(s, "env_log", sizeof(double), (void**)&dlog));
+  TNS_TRY_CUDA(cudaMemsetAsync(dlog, 0, sizeof(double), cx.st));
+  StoredMPS Z;
+  const long long R = cx.R;
+  for (int b = H - 1; b >= 0; --b) {
+    // capacity per site: R * phys * R
+    long long chi = 1;
+    for (int c = 0; c < W; ++c)
+      for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, s->cell[s->cidx(b, c)].dim[leg]);
+    Z.site.assign(W, nullptr);
+    for (int c = 0; c < W; ++c) {
+      char nm[32];
+      snprintf(nm, sizeof nm, "env_Z%d", c);
+      TNS_TRY(wsget(s, nm, cx.esz * R * R * 2 * chi * chi, &Z.site[c]));
+    }
+    ZipSpec ket;
+    ket.S = 1;
+    ket.mview = [&, b](int j) { return mps_view(ec.E[b + 1], W, j, false, 'a', "Dd", 'b', 0, 0); };
+    ket.wview = [&, b](int j) { return cell_view(s, cx.f64, b, j, false, 's', 'u', 'l', 'd', 'r'); };
+    ket.out_phys = "suD";
+    ket.stage = STAGE_ENV_KET;
+    ket.row = b;
+    ket.rev = false;
+    ket.out = &Z;
+    ket.logscale = dlog;
+    TNS_TRY(zip(cx, ket));
+    StoredMPS& Eb = ec.E[b];
+    Eb.site.assign(W, nullptr);
+    long long Du = 1;
+    for (int c = 0; c < W; ++c) Du = std::max<long long>(Du, s->cell[s->cidx(b, c)].dim[LEG_U]);
+    for (int c = 0; c < W; ++c) TNS_TRY_CUDA(cudaMalloc(&Eb.site[c], cx.esz * R * R * Du * Du));
+    ZipSpec bra;
+    bra.S = 1;
+    bra.mview = [&](int j) { return mps_view(Z, W, j, true, 'a', "suD", 'b', 0, 0); };
+    bra.wview = [&, b](int j) { return cell_view(s, cx.f64, b, j, true, 's', 'U', 'l', 'D', 'r', true); };
+    bra.out_phys = "Uu";  // E[b] sites [e][bra][ket][e']
+    bra.stage = STAGE_ENV_BRA;
+    bra.row = b;
+    bra.rev = true;
+    bra.out = &Eb;
+    bra.logscale = dlog;
+    TNS_TRY(zip(cx, bra));
+  }
+  // <psi|psi> = exp(sum of scales) * prod of the (1x1x1x1) sites of E[0]
+  std::vector<double> h(2 * W);
+  for (int c = 0; c < W; ++c) {
+    if (cx.f64) {
+      TNS_TRY_CUDA(cudaMemcpyAsync(&h[2 * c], ec.E[0].site[c], sizeof(cd), cudaMemcpyDeviceToHost, cx.st));
+    } else {
+      float tmp[2];
+      TNS_TRY_CUDA(cudaMemcpyAsync(tmp, ec.E[0].site[c], sizeof(cf), cudaMemcpyDeviceToHost, cx.st));
+      TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+      h[2 * c] = tmp[0];
+      h[2 * c + 1] = tmp[1];
+    }
+  }
+  double lg = 0.0;
+  TNS_TRY_CUDA(cudaMemcpyAsync(&lg, dlog, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
+  TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  double zr = 1.0, zi = 0.0;
+  for (int c = 0; c < W; ++c) {
+    double a = h[2 * c], bb = h[2 * c + 1];
+    double nr = zr * a - zi * bb, ni = zr * bb + zi * a;
+    zr = nr;
+    zi = ni;
+  }
+  ec.log_norm = lg + 0.5 * std::log(zr * zr + zi * zi);
+  ec.valid = true;
+  ec.chi_b = cx.R;
+  ec.prec = prec;
+  ec.version = s->version;
+  return TNS_OK;
+}
+
+static tns_status make_ctx(tns_state* s, int chi_b, uint64_t seed, Ctx& cx) {
+  cx.s = s;
+  cx.st = s->st;
+  cx.f64 = (s->prec == TNS_PREC_FP64);
+  cx.gp = cx.f64 ? Prec::F64 : Prec::F32;
+  cx.gram = cx.f64 ? Prec::F64 : Prec::F32_ACC64;
+  cx.esz = cx.f64 ? sizeof(cd) : sizeof(cf);
+  cx.seed = seed;
+  cx.R = chi_b;
+  return ensure_work_cells(s, cx.f64);
+}
+
+tns_status log_norm(tns_state* s, int chi_b, double* out) {
+  Ctx cx;
+  TNS_TRY(make_ctx(s, chi_b, 0, cx));
+  TNS_TRY(build_envs(cx));
+  *out = s->env.log_norm;
+  return TNS_OK;
+}
+
+// Largest physical/bond dimension of a row.
+static long long row_chi(tns_state* s, int b) {
+  long long chi = 1;
+  for (int c = 0; c < s->W; ++c)
+    for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, s->cell[s->cidx(b, c)].dim[leg]);
+  return chi;
+}
+
+static long long env_rank(const StoredMPS& m) {
+  long long r = 1;
+  for (auto x : m.bond) r = std::max(r, x);
+  return r;
+}
+
+// Per-sample device bytes of the sampler working set (used to pick the chunk).
+static long long sampler_bytes_per_sample(tns_state* s, const Ctx& cx) {
+  long long R = cx.R, chi = 1, rho = 1;
+  for (int b = 0; b < s->H; ++b) chi = std::max(chi, row_chi(s, b));
+  for (auto& E : s->env.E) rho = std::max(rho, env_rank(E));
+  long long kk = R + 8;
+  long long big = R * 2 * R * chi * rho;                 // marginal intermediates
+  long long Tm = R * 2 * chi * R * chi;                  // zip matrix
+  long long site = R * 2 * chi * R;                      // K' site
+  long long per = 2 * big + Tm + 2 * R * 2 * chi * kk + 2 * R * chi * kk + s->W * site * 2 + s->W * R * rho * R +
+                  3 * R * rho * R + 2 * R * chi * R * s->W + R * 4096 * 2 + R * chi * chi * R;
+  return per * (long long)cx.esz + 64 * kk * kk * 16;
+}
+
+tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uint8_t* forced, uint8_t* bits,
+                  double* logq, double* cond) {
+  if (n == 0) return TNS_OK;
+  Ctx cx;
+  TNS_TRY(make_ctx(s, chi_b, seed, cx));
+  TNS_TRY(build_envs(cx));
+  const int H = s->H, W = s->W;
+  TNS_TRY_CUDA(cudaMemsetAsync(logq, 0, sizeof(double) * n, cx.st));
+  // chunk size from free memory
+  size_t fr = 0, tot = 0;
+  TNS_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
+  long long per = sampler_bytes_per_sample(s, cx);
+  long long chunk = std::max<long long>(1, std::min<long long>(n, (long long)(0.45 * (double)fr) / per));
+  chunk = std::min<long long>(chunk, 4096);
+  const long long R = cx.R;
+  long long chimax = 1, rhomax = 1;
+  for (int b = 0; b < H; ++b) chimax = std::max(chimax, row_chi(s, b));
+  for (auto& E : s->env.E) rhomax = std::max(rhomax, env_rank(E));
+  const long long site_cap = R * 2 * chimax * R;         // K' site per sample
+  const long long msite_cap = R * chimax * R;            // projected m site per sample
+  const long long F_cap = R * rhomax * R;
+  const long long big_cap = R * 2 * R * chimax * rhomax;
+  // persistent per-chunk buffers
+  std::vector<void*> Ksite(W), Fs(W + 1), mA(W), mB(W);
+  void *L0, *L1, *Gb, *bigA, *bigB, *ones;
+  for (int j = 0; j < W; ++j) {
+    char nm[32];
+    snprintf(nm, sizeof nm, "s_K%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * site_cap, &Ksite[j]));
+    snprintf(nm, sizeof nm, "s_F%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * F_cap, &Fs[j]));
+    snprintf(nm, sizeof nm, "s_mA%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * msite_cap, &mA[j]));
+    snprintf(nm, sizeof nm, "s_mB%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * msite_cap, &mB[j]));
+  }
+  TNS_TRY(wsget(s, "s_ones", cx.esz * chunk, &ones));
+  Fs[W] = ones;
+  TNS_TRY(wsget(s, "s_L0", cx.esz * chunk * F_cap, &L0));
+  TNS_TRY(wsget(s, "s_L1", cx.esz * chunk * F_cap, &L1));
+  TNS_TRY(wsget(s, "s_G", cx.esz * chunk * 2 * F_cap, &Gb));
+  TNS_TRY(wsget(s, "s_bigA", cx.esz * chunk * big_cap, &bigA));
+  TNS_TRY(wsget(s, "s_bigB", cx.esz * chunk * big_cap, &bigB));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    fill_kernel<C><<<nblk(chunk), 256, 0, cx.st>>>((C*)ones, chunk, 1.0);
+  });
+  s->launches++;
+
+  for (long long s0 = 0; s0 < n; s0 += chunk) {
+    const long long S = std::min(chunk, n - s0);
+    // m_0: trivial, shared by all samples
+    StoredMPS mcur;
+    mcur.reversed = false;
+    mcur.bond.assign(W + 1, 1);
+    mcur.phys.assign(W, {1});
+    mcur.site.assign(W, ones);
+    bool mshared = true;
+    StoredMPS mnext;
+    for (int b = 0; b < H; ++b) {
+      const bool rev = (b % 2 == 1);
+      const bool shared = mshared;            // the row's zip is the same for every sample
+      const long long Sz = shared ? 1 : S;
+      StoredMPS Kp;
+      Kp.site = Ksite;
+      ZipSpec zs;
+      zs.S = Sz;
+      zs.mview = [&, rev, Sz](int j) {
+        long long mst = mshared ? 0 : mps_site_size(mcur, W, j, rev);
+        return mps_view(mcur, W, j, rev, 'a', "u", 'b', Sz, mst);
+      };
+      zs.wview = [&, b, rev](int j) { return cell_view(s, cx.f64, b, j, rev, 's', 'u', 'l', 'd', 'r'); };
+      zs.out_phys = "sd";
+      zs.stage = STAGE_SAMPLE;
+      zs.row = b;
+      zs.rev = rev;
+      zs.out = &Kp;
+      zs.logscale = nullptr;
+      TNS_TRY(zip(cx, zs));
+      const StoredMPS& E = s->env.E[b + 1];
+      auto Eview = [&](int j) { return mps_view(E, W, j, rev, 'e', "Dd", 'f', 0, 0); };
+      auto Kview = [&](int j, char la, char ls, char ld, char lb, long long SS, bool conj) {
+        // K' site j stored [S][k][s][d][k'] in this row's logical order
+        std::string lab = {'S', la, ls, ld, lb};
+        long long sz = Kp.bond[j] * Kp.phys[j][0] * Kp.phys[j][1] * Kp.bond[j + 1];
+        TView v = view(Kp.site[j], lab, {SS, Kp.bond[j], Kp.phys[j][0], Kp.phys[j][1], Kp.bond[j + 1]}, conj);
+        v.stride[0] = shared ? 0 : sz;
+        v.dim[0] = SS;
+        return v;
+      };
+      // right environments F_j, j = W-1..1 (batch Sz)
+      std::vector<long long> fdim(W + 1, 1);
+      for (int j = W - 1; j >= 1; --j) {
+        const long long ka = Kp.bond[j], P = Kp.phys[j][0], Dd = Kp.phys[j][1], kb = Kp.bond[j + 1];
+        TView Ev = Eview(j);
+        const long long re = vdim(Ev, 'e'), rf = vdim(Ev, 'f');
+        // R1: T1[S][a][s][B][d][f] = sum_A K'[a,s,d,A] F_{j+1}[A,f,B]
+        TView Fv = view(Fs[j + 1], "SAfB", {Sz, kb, rf, kb});
+        if (j + 1 == W) Fv.stride[0] = 0;
+        TNS_TRY_CUDA(contract(Kview(j, 'a', 's', 'd', 'A', Sz, false), Fv,
+                              view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), cx.gp, cx.st));
+        // R2: T2[S][a][s][B][e][D] = sum_{d,f} T1 E[e,d,D,f]
+        TNS_TRY_CUDA(contract(view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
+                              view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp, cx.st));
+        // R3: F_j[S][a][e][c] = sum_{s,D,B} T2 conj K'[c,s,D,B]
+        TNS_TRY_CUDA(contract(view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
+                              view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp, cx.st));
+        dispatch(cx.f64, [&](auto* tp) {
+          using C = std::remove_pointer_t<decltype(tp)>;
+          normalize_kernel<C><<<(unsigned)Sz, 256, 0, cx.st>>>((C*)Fs[j], ka * re * ka);
+        });
+        s->launches++;
+        fdim[j] = re;
+      }
+      // left sweep: draw the row's qubits
+      mnext.reversed = rev;
+      mnext.bond = Kp.bond;
+      mnext.phys.assign(W, {});
+      mnext.site = (mcur.site[0] == mA[0]) ? mB : mA;
+      dispatch(cx.f64, [&](auto* tp) {
+        using C = std::remove_pointer_t<decltype(tp)>;
+        fill_kernel<C><<<nblk(S), 256, 0, cx.st>>>((C*)L0, S, 1.0);
+      });
+      s->launches++;
+      void* Lc = L0;
+      void* Ln = L1;
+      for (int j = 0; j < W; ++j) {
+        const long long ka = Kp.bond[j], P = Kp.phys[j][0], Dd = Kp.phys[j][1], kb = Kp.bond[j + 1];
+        TView Ev = Eview(j);
+        const long long re = vdim(Ev, 'e'), rf = vdim(Ev, 'f');
+        // L1: U1[S][c][s][A][e][d] = sum_a L[a,e,c] K'[a,s,d,A]
+        TNS_TRY_CUDA(contract(view(Lc, "Saec", {S, ka, re, ka}), Kview(j, 'a', 's', 'd', 'A', S, false),
+                              view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), cx.gp, cx.st));
+        // L2: U2[S][c][s][A][D][f] = sum_{e,d} U1 E[e,d,D,f]
+        TNS_TRY_CUDA(contract(view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
+                              view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp, cx.st));
+        // L3: G[S][s][A][f][B] = sum_{c,D} U2 conj K'[c,s,D,B]
+        TNS_TRY_CUDA(contract(view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), Kview(j, 'c', 's', 'D', 'B', S, true),
+                              view(Gb, "SsAfB", {S, P, kb, rf, kb}), cx.gp, cx.st));
+        const int c = rev ? W - 1 - j : j;
+        const int q = s->cell[s->cidx(b, c)].qubit;
+        const long long nel = kb * rf * kb;
+        const long long fst = (j + 1 == W || shared) ? 0 : kb * rf * kb;
+        const long long kst = shared ? 0 : ka * P * Dd * kb;
+        dispatch(cx.f64, [&](auto* tp) {
+          using C = std::remove_pointer_t<decltype(tp)>;
+          marginal_kernel<C><<<(unsigned)S, 256, 0, cx.st>>>(
+              (const C*)Gb, (int)P, nel, (const C*)Fs[j + 1], fst, (const C*)Kp.site[j], kst, (int)ka, (int)Dd,
+              (int)kb, (C*)Ln, (C*)mnext.site[j], bits, forced, s->n, q < 0 ? 0 : q, logq, cond, cx.seed, s0);
+        });
+        s->launches++;
+        mnext.phys[j] = {Dd};
+        std::swap(Lc, Ln);
+      }
+      mcur = mnext;
+      mshared = false;
+    }
+  }
+  TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  return TNS_OK;
+}
+
+tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase) {
+  if (n == 0) return TNS_OK;
+  Ctx cx;
+  TNS_TRY(make_ctx(s, chi_b, 0, cx));
+  const int H = s->H, W = s->W;
+  const long long R = cx.R;
+  long long chimax = 1;
+  for (int b = 0; b < H; ++b) chimax = std::max(chimax, row_chi(s, b));
+  size_t fr = 0, tot = 0;
+  TNS_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
+  long long per = (R * chimax * R * W * 2 + R * chimax * R * chimax * 2 + R * 8 * R * chimax * 6) * (long long)cx.esz;
+  long long chunk = std::max<long long>(1, std::min<long long>(n, (long long)(0.4 * (double)fr) / std::max(per, 1LL)));
+  chunk = std::min<long long>(chunk, 16384);
+  const long long msite_cap = R * chimax * R;
+  std::vector<void*> mA(W), mB(W);
+  void* ones;
+  for (int j = 0; j < W; ++j) {
+    char nm[32];
+    snprintf(nm, sizeof nm, "a_mA%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * msite_cap, &mA[j]));
+    snprintf(nm, sizeof nm, "a_mB%d", j);
+    TNS_TRY(wsget(s, nm, cx.esz * chunk * msite_cap, &mB[j]));
+  }
+  TNS_TRY(wsget(s, "a_ones", cx.esz * chunk, &ones));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    fill_kernel<C><<<nblk(chunk), 256, 0, cx.st>>>((C*)ones, chunk, 1.0);
+  });
+  void** dsites;
+  TNS_TRY(wsget(s, "a_sites", sizeof(void*) * W, (void**)&dsites));
+  for (long long s0 = 0; s0 < n; s0 += chunk) {
+    const long long S = std::min(chunk, n - s0);
+    double* la = log_abs + s0;
+    TNS_TRY_CUDA(cudaMemsetAsync(la, 0, sizeof(double) * S, cx.st));
+    StoredMPS mcur;
+    mcur.reversed = false;
+    mcur.bond.assign(W + 1, 1);
+    mcur.phys.assign(W, {1});
+    mcur.site.assign(W, ones);
+    bool first = true;
+    StoredMPS out;
+    for (int b = 0; b < H; ++b) {
+      const bool rev = (b % 2 == 1);
+      out.site = (mcur.site[0] == mA[0]) ? mB : mA;
+      ZipSpec zs;
+      zs.S = S;
+      zs.mview = [&, rev, first](int j) {
+        // per-sample stride of the stored MPS site (0 for the shared trivial row)
+        long long st = first ? 0 : mps_site_size(mcur, W, j, rev);
+        return mps_view(mcur, W, j, rev, 'a', "u", 'b', S, st);
+      };
+      zs.wview = [&, b, rev](int j) {
+        // psi[x_q] projected per sample: the physical axis is replaced by an index offset
+        TView v = cell_view(s, cx.f64, b, j, rev, 's', 'u', 'l', 'd', 'r');
+        int c = rev ? W - 1 - j : j;
+        int q = s->cell[s->cidx(b, c)].qubit;
+        long long sstride = v.stride[0];
+        v.labels.erase(v.labels.begin());
+        v.dim.erase(v.dim.begin());
+        v.stride.erase(v.stride.begin());
+        v.labels.insert(v.labels.begin(), 'S');
+        v.dim.insert(v.dim.begin(), S);
+        v.stride.insert(v.stride.begin(), 0);
+        if (q >= 0) {
+          v.idx = bits + s0 * s->n + q;
+          v.idx_ld = s->n;
+          v.idx_stride = sstride;
+          v.idx_label = 'S';
+        }
+        return v;
+      };
+      zs.out_phys = "d";
+      zs.stage = STAGE_AMPLITUDE;
+      zs.row = b;
+      zs.rev = rev;
+      zs.out = &out;
+      zs.logscale = la;
+      TNS_TRY(zip(cx, zs));
+      for (int j = 0; j < W; ++j)
+        if (out.bond[j] * out.phys[j][0] * out.bond[j + 1] > msite_cap) { set_error("amplitude: site capacity"); return TNS_ERR_STATE; }
+      mcur = out;
+      first = false;
+    }
+    TNS_TRY_CUDA(cudaMemcpyAsync(dsites, mcur.site.data(), sizeof(void*) * W, cudaMemcpyHostToDevice, cx.st));
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      amp_final_kernel<C><<<nblk(S), 256, 0, cx.st>>>((const C* const*)dsites, W, S, la, phase + s0);
+    });
+    s->launches++;
+  }
+  TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  return TNS_OK;
+}
+
+}  // namespace tns

@@ -1,0 +1,105 @@
+// Internal state of the tensor-network library (host side).
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tns.h"
+#include "common.cuh"
+#include "contract.cuh"
+
+namespace tns {
+
+enum Leg { LEG_S = 0, LEG_U = 1, LEG_L = 2, LEG_D = 3, LEG_R = 4 };
+inline int opp_leg(int leg) { return leg == LEG_U ? LEG_D : leg == LEG_D ? LEG_U : leg == LEG_L ? LEG_R : LEG_L; }
+
+// One grid cell: tensor psi[s][u][l][d][r] (FP64 master copy on the device).
+struct Cell {
+  int qubit = -1;            // -1: empty cell (physical dimension 1)
+  int dim[5] = {1, 1, 1, 1, 1};
+  bool edge[5] = {false, false, false, false, false};
+  cd* t = nullptr;           // device, capacity cap complex elements
+  long long cap = 0;
+  long long size() const { return (long long)dim[0] * dim[1] * dim[2] * dim[3] * dim[4]; }
+};
+
+// Named, grow-only device buffers reused across calls.
+struct Workspace {
+  std::map<std::string, std::pair<void*, size_t>> slots;
+  cudaError_t get(const std::string& name, size_t bytes, void** out);
+  void release();
+};
+
+// A boundary MPS stored site by site in the logical order of the sweep that
+// produced it.  Site i has layout [left][phys...][right] in that logical order;
+// `reversed` says whether logical order runs right-to-left over the grid.
+struct StoredMPS {
+  std::vector<void*> site;              // device pointers (working precision)
+  std::vector<long long> bond;          // W+1 bond dims in logical order
+  std::vector<std::vector<long long>> phys;  // per site physical dims (in stored order)
+  bool reversed = false;
+};
+
+struct EnvCache {
+  bool valid = false;
+  int chi_b = 0;
+  int prec = -1;
+  long long version = -1;
+  std::vector<StoredMPS> E;             // E[b], b = 1..H (index b); each stored right-to-left
+  double log_norm = 0.0;
+};
+
+}  // namespace tns
+
+struct tns_state {
+  int H = 0, W = 0, n = 0;
+  bool transposed = false;
+  int chi_max = 1;
+  tns_prec prec = TNS_PREC_MIXED;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  std::vector<tns::Cell> cell;          // H*W, row-major
+  std::vector<int> qcell;               // qubit -> cell index
+  std::vector<cd*> msg;                 // (cell*5 + leg): message into cell across leg, chi_max^2 capacity
+  std::vector<cd*> msg_new;
+  double log_f = 0.0;
+  long long version = 0;                // bumped whenever site tensors change
+  long long launches = 0;
+  tns::Workspace ws;
+  tns::EnvCache env;
+  std::vector<void*> work_cells;        // working-precision copies of the cell tensors
+  int work_prec = -1;
+  long long work_version = -1;
+
+  int cidx(int r, int c) const { return r * W + c; }
+  void nbr(int ci, int leg, int& r2, int& c2) const {
+    int r = ci / W, c = ci % W;
+    r2 = r + (leg == tns::LEG_D) - (leg == tns::LEG_U);
+    c2 = c + (leg == tns::LEG_R) - (leg == tns::LEG_L);
+  }
+};
+
+namespace tns {
+void set_error(const char* fmt, ...);
+tns_status cuda_status(cudaError_t e, const char* where);
+#define TNS_TRY_CUDA(expr)                                         \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return ::tns::cuda_status(_e, #expr);   \
+  } while (0)
+#define TNS_TRY(expr)                      \
+  do {                                     \
+    tns_status _s = (expr);                \
+    if (_s != TNS_OK) return _s;           \
+  } while (0)
+
+// gates.cu
+tns_status apply_gate_layer(tns_state* s, int n_gates, const int32_t* sites, const double* mats, int chi,
+                            double cutoff, double* eps_out);
+tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* resid);
+// sampler.cu
+tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uint8_t* forced, uint8_t* bits,
+                  double* logq, double* cond);
+tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase);
+tns_status log_norm(tns_state* s, int chi_b, double* out);
+}  // namespace tns

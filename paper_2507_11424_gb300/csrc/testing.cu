@@ -1,0 +1,65 @@
+// Test-only entry points (include/tns_testing.h): device primitives exposed
+// through the C ABI so they can be compared with the CPU oracle in isolation.
+#include "../../include/tns_testing.h"
+#include "linalg.cuh"
+#include "state.h"
+
+namespace tns {
+__global__ void philox_test_kernel(long long n, const uint32_t* ck, uint32_t* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t* c = ck + 6 * i;
+  Philox4 w = philox4x32_10(c[0], c[1], c[2], c[3], c[4], c[5]);
+  for (int k = 0; k < 4; ++k) out[4 * i + k] = w.v[k];
+}
+}  // namespace tns
+
+using namespace tns;
+
+extern "C" tns_status tns_test_philox(int64_t n, const uint32_t* ck, uint32_t* out, void* stream) {
+  if (n < 0 || (n > 0 && (!ck || !out))) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  if (n == 0) return TNS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  philox_test_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ck, out);
+  TNS_TRY_CUDA(cudaGetLastError());
+  TNS_TRY_CUDA(cudaStreamSynchronize(st));
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A, double* lam, double* V, void* stream) {
+  if (batch < 0 || n < 1 || n > 256 || !A || !lam || !V) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* work = nullptr;
+  int* status = nullptr;
+  TNS_TRY_CUDA(cudaMalloc(&status, sizeof(int) * (batch > 0 ? batch : 1)));
+  if (!jacobi_fits_smem(n, n)) {
+    long long np = n + (n & 1);
+    TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * 2 * np * np));
+  }
+  cudaError_t e = eigh_batched((cd*)A, (long long)n * n, n, n, batch, lam, (cd*)V, (long long)n * n, work, status, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(work);
+  cudaFree(status);
+  TNS_TRY_CUDA(e);
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_svd(int32_t batch, int32_t m, int32_t n, const double* A, double* s, double* U,
+                                   double* V, void* stream) {
+  if (batch < 0 || n < 1 || m < n || n > 1024 || !A || !s || !U || !V) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* work = nullptr;
+  int* status = nullptr;
+  TNS_TRY_CUDA(cudaMalloc(&status, sizeof(int) * (batch > 0 ? batch : 1)));
+  if (!jacobi_fits_smem(m, n)) {
+    long long np = n + (n & 1);
+    TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * ((long long)m * np + np * np)));
+  }
+  cudaError_t e = svd_batched((cd*)A, (long long)m * n, n, m, n, batch, s, (cd*)U, (long long)m * n, (cd*)V,
+                              (long long)n * n, work, status, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(work);
+  cudaFree(status);
+  TNS_TRY_CUDA(e);
+  return TNS_OK;
+}

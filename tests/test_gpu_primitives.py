@@ -1,0 +1,77 @@
+"""Device primitives through the C ABI against the oracle / numpy (GPU)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2507_11424_gb300 as pkg
+    from paper_2507_11424_gb300 import build
+    build.build()
+    return torch, pkg.load()
+
+
+def _ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def test_device_philox_bit_exact(env):
+    torch, lib = env
+    from oracle import philox
+    rng = np.random.default_rng(0)
+    ck = rng.integers(0, 2**32, size=(4096, 6), dtype=np.uint64)
+    ck[0] = 0
+    ck[1] = 0xFFFFFFFF
+    d_in = torch.tensor(ck.astype(np.uint32).view(np.int32), device="cuda")
+    d_out = torch.zeros((4096, 4), dtype=torch.int32, device="cuda")
+    assert lib.tns_test_philox(4096, _ptr(d_in), _ptr(d_out), None) == 0
+    got = d_out.cpu().numpy().view(np.uint32)
+    ref = np.stack(philox.philox4x32_10(*[ck[:, i] for i in range(6)]), axis=1)
+    assert (got == ref.astype(np.uint32)).all()
+
+
+@pytest.mark.parametrize("n,batch", [(1, 3), (7, 5), (16, 4), (72, 3), (81, 2), (136, 2)])
+def test_device_eigh(env, n, batch):
+    torch, lib = env
+    rng = np.random.default_rng(n)
+    A = rng.normal(size=(batch, n, n)) + 1j * rng.normal(size=(batch, n, n))
+    A = A @ np.conj(np.transpose(A, (0, 2, 1)))            # PSD, like Gram matrices
+    A[0] = A[0] * 1e-3 + np.diag(np.arange(n)) * 0.0        # scaled copy
+    dA = torch.tensor(A.view(np.float64), device="cuda")
+    lam = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
+    V = torch.zeros((batch, n, n, 2), dtype=torch.float64, device="cuda")
+    assert lib.tns_test_eigh(batch, n, _ptr(dA), _ptr(lam), _ptr(V), None) == 0
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy().view(np.complex128).reshape(batch, n, n)
+    for b in range(batch):
+        ref = np.linalg.eigvalsh(A[b])[::-1]
+        scale = np.abs(ref).max()
+        assert np.abs(lam[b] - ref).max() < 1e-12 * scale
+        assert np.abs(V[b].conj().T @ V[b] - np.eye(n)).max() < 1e-12
+        assert np.abs(A[b] @ V[b] - V[b] * lam[b]).max() < 1e-11 * scale
+
+
+@pytest.mark.parametrize("m,n,batch", [(4, 4, 2), (64, 64, 2), (40, 13, 3), (128, 128, 1), (200, 72, 2)])
+def test_device_svd(env, m, n, batch):
+    torch, lib = env
+    rng = np.random.default_rng(m * n)
+    A = rng.normal(size=(batch, m, n)) + 1j * rng.normal(size=(batch, m, n))
+    A[0, :, -1] = A[0, :, 0]                                  # rank deficient
+    dA = torch.tensor(A.view(np.float64), device="cuda")
+    s = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
+    U = torch.zeros((batch, m, n, 2), dtype=torch.float64, device="cuda")
+    V = torch.zeros((batch, n, n, 2), dtype=torch.float64, device="cuda")
+    assert lib.tns_test_svd(batch, m, n, _ptr(dA), _ptr(s), _ptr(U), _ptr(V), None) == 0
+    s = s.cpu().numpy()
+    U = U.cpu().numpy().view(np.complex128).reshape(batch, m, n)
+    V = V.cpu().numpy().view(np.complex128).reshape(batch, n, n)
+    for b in range(batch):
+        ref = np.linalg.svd(A[b], compute_uv=False)
+        assert np.abs(s[b] - ref).max() < 1e-12 * ref[0]
+        rec = (U[b] * s[b]) @ V[b].conj().T
+        assert np.abs(rec - A[b]).max() < 1e-12 * ref[0]
+        assert np.abs(V[b].conj().T @ V[b] - np.eye(n)).max() < 1e-12
