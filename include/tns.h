@@ -163,6 +163,21 @@ tns_status tns_load(const char* path, void* cuda_stream, tns_state** out);
 /* Number of library kernel launches issued since the state was created. */
 tns_status tns_launch_count(const tns_state* s, int64_t* launches);
 
+/*
+ * Kernel timing: when enabled, the sampler brackets each launch of its kernel
+ * classes with CUDA events on the state's stream and accumulates, per class,
+ * the elapsed device time, the launch count and the algorithmic FLOPs (8 per
+ * complex multiply-add of the contraction as written, excluding any padding).
+ * Classes: 0 = environment contractions (the row's norm-environment GEMMs of
+ * the marginal sweeps), 1 = other marginal-sweep contractions, 2 = zip-up
+ * compression contractions, 3 = FP64 Jacobi eigensolves, 4 = fused
+ * marginal/draw/project kernel.  tns_profile_enable(s, 1) also clears the
+ * counters.
+ */
+tns_status tns_profile_enable(tns_state* s, int32_t enable);
+tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_ms, int64_t* launches,
+                            double* flops);
+
 void tns_destroy(tns_state* s);
 const char* tns_last_error(void);
 

@@ -15,8 +15,8 @@ following the paper's Appendix "Sampling from a Tensor Network State" (Fig. 7):
 
 The MPS-MPO compression is a zip-up sweep whose per-site truncated SVD is taken
 by the randomized range finder (Halko, Martinsson, Tropp 2011, Alg. 4.4: a
-shared Philox test matrix, one subspace iteration, then an SVD of the projected
-matrix): the rank-R
+shared Philox test matrix, one subspace iteration with an orthonormalisation
+after every application, then an SVD of the projected matrix): the rank-R
 truncation that the library computes.  When R + oversampling covers the full
 column dimension the test matrix is the identity and the step is an exact
 truncated SVD.  ``zip_compress(exact=True)`` takes the plain SVD instead and is
@@ -37,6 +37,13 @@ from . import philox
 
 OVERSAMPLE = 8
 POWER_ITERS = 1
+# Shift of the Cholesky orthonormalisation of a range-finder basis, relative to
+# the largest diagonal entry of its Gram matrix (FP64 algorithm).  The library's
+# mixed-precision path uses ORTH_SHIFT_MIXED; pass gram_cut=ORTH_SHIFT_MIXED to
+# replay it.
+ORTH_SHIFT = 1e-14
+ORTH_SHIFT_MIXED = 1e-8
+GRAM_CUT, GRAM_CUT_MIXED = ORTH_SHIFT, ORTH_SHIFT_MIXED
 
 
 # ---------------------------------------------------------------- small helpers
@@ -67,29 +74,31 @@ def eigh_desc(A: np.ndarray):
     return lam[::-1], V[:, ::-1]
 
 
-def orth(Y: np.ndarray, gram_cut: float) -> np.ndarray:
-    """Orthonormal basis Q = Y V Lambda^{-1/2} of range(Y) from the Gram matrix Y^H Y.
+def orth(Y: np.ndarray, shift: float) -> np.ndarray:
+    """Orthonormal basis Q = Y L^{-H} of range(Y), with L L^H = Y^H Y + shift * max_i G_ii * I.
 
-    Eigen-directions with lambda <= gram_cut * lambda_max are dropped.
+    The shift keeps the Cholesky factorisation defined for rank-deficient Y and
+    damps directions whose Gram eigenvalue is below shift * max_i G_ii.
     """
-    lam, V = eigh_desc(Y.conj().T @ Y)
-    if lam[0] <= 0:
-        return np.zeros((Y.shape[0], 0), dtype=np.complex128)
-    keep = lam > gram_cut * lam[0]
-    return Y @ (V[:, keep] / np.sqrt(lam[keep]))
+    G = Y.conj().T @ Y
+    m = float(np.max(np.real(np.diag(G)))) if G.size else 0.0
+    if m <= 0:
+        return np.zeros_like(Y)
+    L = np.linalg.cholesky(G + shift * m * np.eye(G.shape[0]))
+    return np.linalg.solve(L, Y.conj().T).conj().T          # Y L^{-H}
 
 
-def truncate(T: np.ndarray, R: int, omega, gram_cut: float = 1e-12, exact: bool = False,
+def truncate(T: np.ndarray, R: int, omega, gram_cut: float = ORTH_SHIFT, exact: bool = False,
              power_iters: int = POWER_ITERS):
     """Rank-R factorisation T ~ K C with K having orthonormal columns (the "QR + truncated SVD").
 
-    Randomized range finder with subspace iteration (Halko, Martinsson, Tropp
-    2011, Alg. 4.4): Y = T Omega, then ``power_iters`` times Y = T T^H orth(Y);
-    Omega = I (and no iteration) when k = R + p >= N, which makes the step an exact
-    truncated SVD.  Then Q = orth(Y), B = Q^H T, B B^H = U_B S^2 U_B^H, and
-    K = Q U_B[:, :R], C = K^H T.  Column phases of K follow ``fix_phase``.  K and C
-    depend only on range(Y) and T, not on the basis an implementation picks.
-    Returns K (M x Rk), C (Rk x N), Rk = min(R, M, N); unused columns are zero.
+    Randomized range finder with subspace iteration, orthonormalising after every
+    application (Halko, Martinsson, Tropp 2011, Alg. 4.4): Y = T Omega, then
+    ``power_iters`` times Y = T orth(T^H orth(Y)); Omega = I (and no iteration)
+    when k = R + p >= N, which makes the step an exact truncated SVD.  Then
+    Q = orth(Y), B = Q^H T, B B^H = U_B S^2 U_B^H, K = Q U_B[:, :R], C = K^H T.
+    Column phases of K follow ``fix_phase``.  ``gram_cut`` is the orthonormalisation
+    shift.  Returns K (M x Rk), C (Rk x N), Rk = min(R, M, N).
     """
     M, N = T.shape
     Rk = min(R, M, N)
@@ -105,10 +114,9 @@ def truncate(T: np.ndarray, R: int, omega, gram_cut: float = 1e-12, exact: bool 
     else:
         Y = T @ omega(N, kk)
         for _ in range(power_iters):
-            Y = T @ (T.conj().T @ orth(Y, gram_cut))
+            Z = orth(T.conj().T @ orth(Y, gram_cut), gram_cut)
+            Y = T @ Z
     Q = orth(Y, gram_cut)
-    if Q.shape[1] == 0:
-        return K, np.zeros((Rk, N), dtype=np.complex128)
     B = Q.conj().T @ T
     mu, UB = eigh_desc(B @ B.conj().T)
     n = min(Rk, UB.shape[1])
@@ -116,7 +124,7 @@ def truncate(T: np.ndarray, R: int, omega, gram_cut: float = 1e-12, exact: bool 
     return K, K.conj().T @ T
 
 
-def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=1e-12):
+def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT):
     """Zip-up MPS-MPO compression to rank R along the given (logical) site order.
 
     T_j[(k, y, xp), (a', r)] = sum C_{j-1}[k, a, l] m_j[a, xc, xp, a'] w_j[l, xc, y, r];
@@ -169,7 +177,7 @@ def row_cells(tns, b, reverse):
 ENV_SEED = 0
 
 
-def norm_envs(tns, R, seed=ENV_SEED, gram_cut=1e-12, exact=False):
+def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False):
     """Bottom environments E[b] of <psi|psi> for b = 1..H (E[H] trivial).
 
     E[b] is stored in column order with sites E[b][c][e, d, dbar, e'] on the
@@ -210,7 +218,7 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=1e-12, exact=False):
 
 
 # ------------------------------------------------------------------- sampler
-def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=1e-12, exact=False):
+def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=ORTH_SHIFT, exact=False):
     """One partition: absorb + compress, right environments, draw left to right.
 
     m: MPS m[a, u, 1, a'] in this row's logical order; row: psi sites in logical
@@ -259,7 +267,7 @@ def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=1e-1
     return bits, q0s, logq, m_next
 
 
-def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram_cut=1e-12, exact=False):
+def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram_cut=ORTH_SHIFT, exact=False):
     """Draw samples (or replay ``forced`` bitstrings); returns bits [n, n_qubits], log q, q0.
 
     q0[n, qubit] is the conditional probability of 0 that the draw of that qubit used.
@@ -295,7 +303,7 @@ def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram
     return bits_out, logq, q0_out
 
 
-def amplitude(tns, R, bits, seed, gram_cut=1e-12, exact=False):
+def amplitude(tns, R, bits, seed, gram_cut=ORTH_SHIFT, exact=False):
     """<x|psi> by single-layer boundary MPS over projected rows; returns (log|a|, phase)."""
     H, W = tns.H, tns.W
     m = [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]

@@ -133,6 +133,19 @@ class TNSState:
         check(self.lib.tns_launch_count(self._h, C.byref(v)), "tns_launch_count")
         return v.value
 
+    PROFILE_CLASSES = ("env_gemm", "sweep_gemm", "zip_gemm", "eigh", "marginal")
+
+    def profile(self, enable: bool = True):
+        check(self.lib.tns_profile_enable(self._h, 1 if enable else 0), "tns_profile_enable")
+
+    def profile_read(self):
+        out = {}
+        for i, name in enumerate(self.PROFILE_CLASSES):
+            ms, n, fl = C.c_double(), C.c_int64(), C.c_double()
+            check(self.lib.tns_profile_read(self._h, i, C.byref(ms), C.byref(n), C.byref(fl)), "tns_profile_read")
+            out[name] = dict(ms=ms.value, launches=n.value, flops=fl.value)
+        return out
+
     # ---------------------------------------------------------------- sampling
     def sample(self, chi_b: int, n: int, seed: int, n_sites: int | None = None, cond: bool = False, out=None):
         """Draw n samples; returns torch CUDA tensors (bits uint8 [n, n_sites], logq f64 [n][, cond])."""

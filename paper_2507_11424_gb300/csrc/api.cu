@@ -43,6 +43,41 @@ cudaError_t Workspace::get(const std::string& name, size_t bytes, void** out) {
   return cudaSuccess;
 }
 
+cudaEvent_t Profiler::begin(cudaStream_t st) {
+  if (!on) return nullptr;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, st);
+  return e;
+}
+
+void Profiler::end(int cls, cudaEvent_t a, double fl, cudaStream_t st) {
+  if (!on || !a) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaEventDestroy(a); return; }
+  cudaEventRecord(e, st);
+  pending.push_back({cls, a, e, fl});
+}
+
+void Profiler::resolve() {
+  for (auto& r : pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ms[r.cls] += t;
+      flops[r.cls] += r.flops;
+      n[r.cls] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  pending.clear();
+}
+
+void Profiler::clear() {
+  resolve();
+  for (int i = 0; i < NCLASS; ++i) { ms[i] = 0; flops[i] = 0; n[i] = 0; }
+}
+
 void Workspace::release() {
   for (auto& kv : slots) cudaFree(kv.second.first);
   slots.clear();
@@ -54,33 +89,40 @@ __global__ void init_product_kernel(cd* t, int bit) {
 }
 __global__ void fill_one_kernel(cd* t) { t[0] = mk(1.0, 0.0); }
 
+// Cells and messages live in two arenas so batched kernels can gather them by offset.
 static tns_status alloc_state(tns_state* s) {
   const int nc = s->H * s->W;
   s->msg.assign((size_t)nc * 5, nullptr);
   s->msg_new.assign((size_t)nc * 5, nullptr);
+  long long total = 0;
   for (int ci = 0; ci < nc; ++ci) {
     Cell& c = s->cell[ci];
     long long cap = (c.qubit >= 0) ? 2 : 1;
     for (int leg = 1; leg <= 4; ++leg) cap *= c.edge[leg] ? s->chi_max : 1;
     c.cap = cap;
-    TNS_TRY_CUDA(cudaMalloc(&c.t, sizeof(cd) * cap));
+    c.off = total;
+    total += (cap + 31) / 32 * 32;
+  }
+  TNS_TRY_CUDA(cudaMalloc(&s->cell_arena, sizeof(cd) * total));
+  const long long mslot = (long long)s->chi_max * s->chi_max;
+  TNS_TRY_CUDA(cudaMalloc(&s->msg_arena, sizeof(cd) * mslot * nc * 5));
+  TNS_TRY_CUDA(cudaMalloc(&s->msg_new_arena, sizeof(cd) * mslot * nc * 5));
+  for (int ci = 0; ci < nc; ++ci) {
+    Cell& c = s->cell[ci];
+    c.t = s->cell_arena + c.off;
     for (int leg = 1; leg <= 4; ++leg) {
       if (!c.edge[leg]) continue;
-      size_t mb = sizeof(cd) * (size_t)s->chi_max * s->chi_max;
-      TNS_TRY_CUDA(cudaMalloc(&s->msg[ci * 5 + leg], mb));
-      TNS_TRY_CUDA(cudaMalloc(&s->msg_new[ci * 5 + leg], mb));
+      s->msg[ci * 5 + leg] = s->msg_arena + (long long)(ci * 5 + leg) * mslot;
+      s->msg_new[ci * 5 + leg] = s->msg_new_arena + (long long)(ci * 5 + leg) * mslot;
     }
   }
   return TNS_OK;
 }
 
 static void free_state(tns_state* s) {
-  for (auto& c : s->cell)
-    if (c.t) cudaFree(c.t);
-  for (auto p : s->msg)
-    if (p) cudaFree(p);
-  for (auto p : s->msg_new)
-    if (p) cudaFree(p);
+  if (s->cell_arena) cudaFree(s->cell_arena);
+  if (s->msg_arena) cudaFree(s->msg_arena);
+  if (s->msg_new_arena) cudaFree(s->msg_new_arena);
   for (auto p : s->work_cells)
     if (p) cudaFree(p);
   for (auto& E : s->env.E)
@@ -278,6 +320,24 @@ extern "C" tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int3
 extern "C" tns_status tns_launch_count(const tns_state* s, int64_t* launches) {
   if (!s || !launches) { set_error("invalid argument"); return TNS_ERR_ARG; }
   *launches = s->launches + contract_launches();
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_profile_enable(tns_state* s, int32_t enable) {
+  if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
+  TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
+  s->prof.clear();
+  s->prof.on = enable != 0;
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_profile_read(tns_state* s, int32_t cls, double* ms, int64_t* launches, double* flops) {
+  if (!s || cls < 0 || cls >= Profiler::NCLASS) { set_error("invalid argument to tns_profile_read"); return TNS_ERR_ARG; }
+  TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
+  s->prof.resolve();
+  if (ms) *ms = s->prof.ms[cls];
+  if (launches) *launches = s->prof.n[cls];
+  if (flops) *flops = s->prof.flops[cls];
   return TNS_OK;
 }
 

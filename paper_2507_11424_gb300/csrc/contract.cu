@@ -45,6 +45,10 @@ struct GemmParams {
   const uint8_t* bidx;
   long long b_idx_ld, b_idx_stride;
   int b_idx_grp;
+  const long long* aoff;
+  const long long* boffs;
+  const long long* coff;
+  int aoff_grp, boff_grp, coff_grp;
   const void* A;
   const void* B;
   void* C;
@@ -52,6 +56,10 @@ struct GemmParams {
   double2 alpha, beta;
   int beta_zero;
   int a_kfast, b_kfast;
+  // split-K: blocks of one output tile share blockIdx.x/y and split the K loop;
+  // partial tiles go to `partial` and a second kernel reduces them in order
+  int splits, kchunk;
+  void* partial;
 };
 
 template <typename T> __device__ inline T ld_in(const T* p, bool cj) {
@@ -99,8 +107,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
 
   long long offA = 0, offB = 0, offC = 0;
   int bi[2] = {0, 0};
+  const int ks = blockIdx.z % p.splits;
+  const int bz = blockIdx.z / p.splits;
   {
-    int r = blockIdx.z;
+    int r = bz;
     for (int g = 0; g < p.nb; ++g) {
       bi[g] = r % p.bdim[g];
       r /= p.bdim[g];
@@ -111,6 +121,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
   }
   if (p.aidx) offA += (long long)p.aidx[(long long)bi[p.a_idx_grp] * p.a_idx_ld] * p.a_idx_stride;
   if (p.bidx) offB += (long long)p.bidx[(long long)bi[p.b_idx_grp] * p.b_idx_ld] * p.b_idx_stride;
+  if (p.aoff) offA += p.aoff[bi[p.aoff_grp]];
+  if (p.boffs) offB += p.boffs[bi[p.boff_grp]];
+  if (p.coff) offC += p.coff[bi[p.coff_grp]];
   const TI* A = (const TI*)p.A + offA;
   const TI* B = (const TI*)p.B + offB;
   TO* C = (TO*)p.C + offC;
@@ -151,11 +164,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
     for (int j = 0; j < 4; ++j) acc[i][j] = czero<TACC>();
 
   const bool cjA = p.conjA != 0, cjB = p.conjB != 0;
-  for (int k0 = 0; k0 < p.K; k0 += BK) {
+  const int kbeg = ks * p.kchunk;
+  const int kend = min(p.K, kbeg + p.kchunk);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     __syncthreads();
     if (tid < BK) {
       long long k = k0 + tid, oa = 0, ob = 0;
-      if (k < p.K) {
+      if (k < kend) {
         long long r = k;
         for (int g = 0; g < p.nk; ++g) {
           long long i = r % p.kdim[g];
@@ -172,14 +187,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
       int mm, kk;
       if (p.a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
       TI v = czero<TI>();
-      if (m0 + mm < p.M && k0 + kk < p.K) v = ld_in(A + rowA[mm] + kA[kk], cjA);
+      if (m0 + mm < p.M && k0 + kk < kend) v = ld_in(A + rowA[mm] + kA[kk], cjA);
       As[kk][mm] = v;
     }
     for (int e = tid; e < BN * BK; e += 256) {
       int nn, kk;
       if (p.b_kfast) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
       TI v = czero<TI>();
-      if (n0 + nn < p.N && k0 + kk < p.K) v = ld_in(B + kB[kk] + colB[nn], cjB);
+      if (n0 + nn < p.N && k0 + kk < kend) v = ld_in(B + kB[kk] + colB[nn], cjB);
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -197,6 +212,16 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
     }
   }
 
+  if (p.splits > 1) {
+    TACC* part = (TACC*)p.partial +
+                 (((long long)bz * p.splits + ks) * gridDim.x * gridDim.y + (long long)blockIdx.x * gridDim.y +
+                  blockIdx.y) * (BM * BN);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[(ty + 16 * i) * BN + tx + 16 * j] = acc[i][j];
+    return;
+  }
   TACC al = narrow<TACC>(p.alpha), be = narrow<TACC>(p.beta);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -211,6 +236,45 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmParams p) {
       if (!p.beta_zero) v = cadd(v, cmul(be, widen(*dst, TACC())));
       *dst = narrow<TO>(v);
     }
+  }
+}
+
+// Sums the split-K partial tiles in a fixed order (deterministic) and writes C.
+template <typename TACC, typename TO>
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(const GemmParams p, unsigned gx, unsigned gy) {
+  const long long tile = blockIdx.x;                 // over batch * gx * gy
+  const long long bz = tile / ((long long)gx * gy);
+  const long long txy = tile % ((long long)gx * gy);
+  const long long bx = txy / gy, by = txy % gy;
+  long long offC = 0;
+  int bi[2] = {0, 0};
+  {
+    long long r = bz;
+    for (int g = 0; g < p.nb; ++g) {
+      bi[g] = (int)(r % p.bdim[g]);
+      r /= p.bdim[g];
+      offC += bi[g] * p.sCb[g];
+    }
+  }
+  if (p.coff) offC += p.coff[bi[p.coff_grp]];
+  TO* C = (TO*)p.C + offC;
+  const TACC* part = (const TACC*)p.partial;
+  TACC al = narrow<TACC>(p.alpha), be = narrow<TACC>(p.beta);
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    long long m = bx * 64 + e / 64;
+    long long n = by * 64 + e % 64;
+    if (m >= p.M || n >= p.N) continue;
+    TACC acc = czero<TACC>();
+    for (int ks = 0; ks < p.splits; ++ks)
+      acc = cadd(acc, part[((bz * p.splits + ks) * gx * gy + bx * gy + by) * 4096 + e]);
+    long long oc = 0, r = m;
+    for (int g = 0; g < p.nm; ++g) { oc += (r % p.mdim[g]) * p.sCm[g]; r /= p.mdim[g]; }
+    r = n;
+    for (int g = 0; g < p.nn; ++g) { oc += (r % p.ndim[g]) * p.sCn[g]; r /= p.ndim[g]; }
+    TO* dst = C + oc;
+    TACC v = cmul(al, acc);
+    if (!p.beta_zero) v = cadd(v, cmul(be, widen(*dst, TACC())));
+    *dst = narrow<TO>(v);
   }
 }
 
@@ -247,7 +311,8 @@ std::vector<Grp> merge(std::vector<Grp> g, int nops) {
 }  // namespace
 
 cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st, double2 alpha,
-                     double2 beta) {
+                     double2 beta, double* flops_out) {
+  if (flops_out) *flops_out = 0.0;
   std::vector<Lab> labs;
   auto find = [&](char c) -> Lab& {
     for (auto& l : labs)
@@ -274,12 +339,15 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
   }
   std::vector<Grp> gm, gn, gk, gb;
   char a_idx_label = A.idx ? A.idx_label : 0, b_idx_label = B.idx ? B.idx_label : 0;
+  std::string off_labels;
+  for (const TView* v : {&A, &B, &C})
+    if (v->boff && off_labels.find(v->boff_label) == std::string::npos) off_labels.push_back(v->boff_label);
   std::vector<Grp> gb_idx;  // batch labels carrying an index offset (kept unmerged, first)
   std::vector<char> gb_idx_lab;
   long long Mtot = 1, Ntot = 1, Ktot = 1;
   for (auto& l : labs) {
     if (l.d == 0) return cudaSuccess;  // empty contraction or empty output
-    bool idxl = (l.c == a_idx_label || l.c == b_idx_label);
+    bool idxl = (l.c == a_idx_label || l.c == b_idx_label || off_labels.find(l.c) != std::string::npos);
     if (l.d == 1 && !idxl) continue;
     if (l.inA && l.inB && l.inC) {
       if (idxl) { gb_idx.push_back(Grp{l.d, l.sc, l.sa, l.sb}); gb_idx_lab.push_back(l.c); }
@@ -332,6 +400,13 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
     if (gb_idx_lab[i] == b_idx_label) { p.bidx = B.idx; p.b_idx_ld = B.idx_ld; p.b_idx_stride = B.idx_stride; p.b_idx_grp = (int)i; }
   }
   if ((A.idx && !p.aidx) || (B.idx && !p.bidx)) return cudaErrorInvalidValue;
+  p.aoff = p.boffs = p.coff = nullptr;
+  for (size_t i = 0; i < gb_idx_lab.size(); ++i) {
+    if (A.boff && gb_idx_lab[i] == A.boff_label) { p.aoff = A.boff; p.aoff_grp = (int)i; }
+    if (B.boff && gb_idx_lab[i] == B.boff_label) { p.boffs = B.boff; p.boff_grp = (int)i; }
+    if (C.boff && gb_idx_lab[i] == C.boff_label) { p.coff = C.boff; p.coff_grp = (int)i; }
+  }
+  if ((A.boff && !p.aoff) || (B.boff && !p.boffs) || (C.boff && !p.coff)) return cudaErrorInvalidValue;
   p.A = A.ptr;
   p.B = B.ptr;
   p.C = C.ptr;
@@ -354,16 +429,42 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
     p.b_kfast = (p.sBk[0] == 1 && !(p.nn > 0 && p.sBn[0] == 1));
   }
   if (p.M == 0 || p.N == 0) return cudaSuccess;
+  if (flops_out) *flops_out = 8.0 * (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
   long long gx = (p.M + 63) / 64;
   int gy = (p.N + 63) / 64;
   if (gx > 2147483647LL || gy > 65535) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nbatch);
+  // split K when the output has too few tiles to fill the GPU
+  const long long tiles = gx * gy * nbatch;
+  int splits = 1;
+  if (tiles < 2 * 152 && p.K >= 1024) {
+    splits = (int)std::min<long long>(std::min<long long>(64, p.K / 512), (4 * 152 + tiles - 1) / tiles);
+    splits = std::max(1, std::min<int>(splits, (int)(65535 / std::max<long long>(1, nbatch))));
+  }
+  const int bk = (prec == Prec::F32) ? 16 : 8;
+  p.splits = splits;
+  p.kchunk = splits > 1 ? (int)(((p.K + splits - 1) / splits + bk - 1) / bk * bk) : p.K;
+  p.partial = nullptr;
+  const size_t acc_bytes = (prec == Prec::F32) ? sizeof(float2) : sizeof(double2);
+  if (splits > 1) {
+    cudaError_t e = cudaMallocAsync(&p.partial, acc_bytes * 4096 * (size_t)tiles * splits, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(nbatch * splits));
   switch (prec) {
     case Prec::F64: gemm_kernel<double2, double2, double2, 8><<<grid, 256, 0, st>>>(p); break;
     case Prec::F32: gemm_kernel<float2, float2, float2, 16><<<grid, 256, 0, st>>>(p); break;
     case Prec::F32_ACC64: gemm_kernel<float2, double2, double2, 8><<<grid, 256, 0, st>>>(p); break;
   }
   g_launches++;
+  if (splits > 1) {
+    switch (prec) {
+      case Prec::F64: splitk_reduce_kernel<double2, double2><<<(unsigned)tiles, 256, 0, st>>>(p, (unsigned)gx, gy); break;
+      case Prec::F32: splitk_reduce_kernel<float2, float2><<<(unsigned)tiles, 256, 0, st>>>(p, (unsigned)gx, gy); break;
+      case Prec::F32_ACC64: splitk_reduce_kernel<double2, double2><<<(unsigned)tiles, 256, 0, st>>>(p, (unsigned)gx, gy); break;
+    }
+    g_launches++;
+    cudaFreeAsync(p.partial, st);
+  }
   return cudaGetLastError();
 }
 

@@ -26,6 +26,10 @@ struct TView {
   const uint8_t* idx = nullptr;
   long long idx_ld = 0, idx_stride = 0;
   char idx_label = 0;
+  // optional per-batch element offsets (device int64): ptr += boff[b] where b is the
+  // index of batch label boff_label (gathers operands that are not equally spaced)
+  const long long* boff = nullptr;
+  char boff_label = 0;
 };
 
 // Row-major contiguous view helper.
@@ -35,8 +39,10 @@ TView& bcast(TView& v, char label, long long dim);
 
 // C = alpha * sum_K A * B + beta * C  (labels of C decide the output layout).
 // Returns cudaSuccess or an error; throws nothing.
+// flops_out (optional) receives 8 * M * N * K * batch, the algorithmic real FLOPs.
 cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st,
-                     double2 alpha = make_double2(1.0, 0.0), double2 beta = make_double2(0.0, 0.0));
+                     double2 alpha = make_double2(1.0, 0.0), double2 beta = make_double2(0.0, 0.0),
+                     double* flops_out = nullptr);
 
 // Number of GEMM launches issued so far (for launch accounting).
 long long contract_launches();

@@ -2,6 +2,7 @@
 // propagation (Appendix Fig. 8c) on the device, FP64 throughout.
 #include <cctype>
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -399,25 +400,75 @@ tns_status apply_gate_layer(tns_state* s, int n_gates, const int32_t* sites, con
 }
 
 // ---------------------------------------------------------------- BP
+// Directed edges (v -> v') are grouped by the shape of psi_v and the outgoing
+// leg; each group runs as one batched contraction chain that gathers the cell
+// tensors and messages of its members through per-member offset arrays:
+//   X = psi_v x_l m_{l -> v} for every other bonded leg l, then
+//   m_new[k, kbar] = sum X[.. k ..] conj(psi_v[.. kbar ..]).
 tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* resid) {
   cudaStream_t st = s->st;
-  GateBufs b;
-  TNS_TRY(gate_buffers(s, b));
-  struct DirEdge { int ci, j, dst; };
-  std::vector<DirEdge> de;
+  struct Group {
+    int dims[5];
+    int edges;
+    int j;
+    std::vector<long long> cell_off, dst_off, moff[5];
+    long long* d_cell = nullptr;
+    long long* d_dst = nullptr;
+    long long* d_moff[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  };
+  std::vector<Group> groups;
   std::vector<MsgDesc> md;
-  for (int ci = 0; ci < (int)s->cell.size(); ++ci)
+  const long long mslot = (long long)s->chi_max * s->chi_max;
+  for (int ci = 0; ci < (int)s->cell.size(); ++ci) {
+    const Cell& c = s->cell[ci];
+    int eb = 0;
+    for (int leg = 1; leg <= 4; ++leg) eb |= (c.edge[leg] ? 1 : 0) << leg;
     for (int j = 1; j <= 4; ++j) {
-      if (!s->cell[ci].edge[j]) continue;
+      if (!c.edge[j]) continue;
       int r2, c2;
       s->nbr(ci, j, r2, c2);
       int dst = s->cidx(r2, c2) * 5 + opp_leg(j);
-      de.push_back({ci, j, dst});
-      md.push_back({s->msg[dst], s->msg_new[dst], s->cell[ci].dim[j]});
+      Group* g = nullptr;
+      for (auto& gg : groups)
+        if (gg.j == j && gg.edges == eb && std::equal(gg.dims, gg.dims + 5, c.dim)) { g = &gg; break; }
+      if (!g) {
+        groups.emplace_back();
+        g = &groups.back();
+        std::copy(c.dim, c.dim + 5, g->dims);
+        g->edges = eb;
+        g->j = j;
+      }
+      g->cell_off.push_back(c.off);
+      g->dst_off.push_back((long long)dst * mslot);
+      for (int leg = 1; leg <= 4; ++leg) g->moff[leg].push_back((long long)(ci * 5 + leg) * mslot);
+      md.push_back({s->msg[dst], s->msg_new[dst], c.dim[j]});
     }
+  }
   *iters = 0;
   *resid = 0.0;
-  if (de.empty()) return TNS_OK;
+  if (md.empty()) return TNS_OK;
+  // upload the offset tables once
+  std::vector<long long> table;
+  for (auto& g : groups) {
+    table.insert(table.end(), g.cell_off.begin(), g.cell_off.end());
+    table.insert(table.end(), g.dst_off.begin(), g.dst_off.end());
+    for (int leg = 1; leg <= 4; ++leg) table.insert(table.end(), g.moff[leg].begin(), g.moff[leg].end());
+  }
+  long long* dtab = nullptr;
+  TNS_TRY_CUDA(s->ws.get("bp_tab", sizeof(long long) * table.size(), (void**)&dtab));
+  TNS_TRY_CUDA(cudaMemcpyAsync(dtab, table.data(), sizeof(long long) * table.size(), cudaMemcpyHostToDevice, st));
+  long long pos = 0, xmax = 1;
+  for (auto& g : groups) {
+    const long long G = (long long)g.cell_off.size();
+    g.d_cell = dtab + pos; pos += G;
+    g.d_dst = dtab + pos; pos += G;
+    for (int leg = 1; leg <= 4; ++leg) { g.d_moff[leg] = dtab + pos; pos += G; }
+    long long sz = (long long)g.dims[0] * g.dims[1] * g.dims[2] * g.dims[3] * g.dims[4];
+    xmax = std::max(xmax, G * sz);
+  }
+  cd *X0, *X1;
+  TNS_TRY_CUDA(s->ws.get("bp_X0", sizeof(cd) * xmax, (void**)&X0));
+  TNS_TRY_CUDA(s->ws.get("bp_X1", sizeof(cd) * xmax, (void**)&X1));
   MsgDesc* dmd = nullptr;
   double* dres = nullptr;
   TNS_TRY_CUDA(s->ws.get("bp_desc", sizeof(MsgDesc) * md.size(), (void**)&dmd));
@@ -426,24 +477,47 @@ tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* 
   std::vector<double> hres(md.size());
   const std::string lab = "suldr";
   for (int it = 1; it <= max_iter; ++it) {
-    for (auto& e : de) {
-      const Cell& c = s->cell[e.ci];
-      cd* bufs[2] = {b.t1, b.t2};
-      const cd* cur = c.t;
+    for (auto& g : groups) {
+      const long long G = (long long)g.cell_off.size();
+      std::vector<long long> d5 = dims5(g.dims);
+      std::vector<long long> gd = {G};
+      gd.insert(gd.end(), d5.begin(), d5.end());
+      const long long sz = d5[0] * d5[1] * d5[2] * d5[3] * d5[4];
+      // current operand: the cells themselves (gathered) or a workspace buffer
+      TView cur = view(s->cell_arena, "G" + lab, gd);
+      cur.stride[0] = 0;
+      cur.boff = g.d_cell;
+      cur.boff_label = 'G';
+      cd* bufs[2] = {X0, X1};
       int nb = 0;
       for (int leg = 1; leg <= 4; ++leg) {
-        if (leg == e.j || !c.edge[leg]) continue;
+        if (leg == g.j || !(g.edges >> leg & 1)) continue;
+        std::string out = "G" + lab;
+        out[leg + 1] = (char)toupper(lab[leg]);
+        TView M = view(s->msg_arena, std::string("G") + lab[leg] + out[leg + 1], {G, d5[leg], d5[leg]});
+        M.stride[0] = 0;
+        M.boff = g.d_moff[leg];
+        M.boff_label = 'G';
         cd* dst = bufs[nb & 1];
-        TNS_TRY_CUDA(apply_leg(cur, c.dim, leg, s->msg[e.ci * 5 + leg], dst, st));
-        cur = dst;
+        TNS_TRY_CUDA(contract(cur, M, view(dst, out, gd), Prec::F64, st));
+        cur = view(dst, "G" + lab, gd);   // labels restart for the next leg
         ++nb;
       }
-      std::string la = lab, lb = lab;
-      la[e.j] = 'a';
-      lb[e.j] = 'b';
-      int D = c.dim[e.j];
-      TNS_TRY_CUDA(contract(view((void*)cur, la, dims5(c.dim)), view(c.t, lb, dims5(c.dim), true),
-                            view(s->msg_new[e.dst], "ab", {D, D}), Prec::F64, st));
+      std::string la = "G" + lab, lb = "G" + lab;
+      la[g.j + 1] = 'a';
+      lb[g.j + 1] = 'b';
+      cur.labels = la;
+      TView bra = view(s->cell_arena, lb, gd, true);
+      bra.stride[0] = 0;
+      bra.boff = g.d_cell;
+      bra.boff_label = 'G';
+      const long long D = d5[g.j];
+      TView out = view(s->msg_new_arena, "Gab", {G, D, D});
+      out.stride[0] = 0;
+      out.boff = g.d_dst;
+      out.boff_label = 'G';
+      TNS_TRY_CUDA(contract(cur, bra, out, Prec::F64, st));
+      (void)sz;
     }
     bp_finish_kernel<<<(unsigned)md.size(), 256, 0, st>>>(dmd, dres);
     s->launches++;

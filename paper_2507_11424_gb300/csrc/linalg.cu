@@ -51,10 +51,10 @@ __device__ inline double warp_max(double v) {
 
 __global__ void __launch_bounds__(JAC_THREADS)
 eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long long sV, cd* work, int* status,
-            int use_smem) {
+            int use_smem, int* sweeps_out) {
   extern __shared__ double4 smraw4[];
-  __shared__ double cs_c[128], cs_s[128], cs_d[128];
-  __shared__ cd cs_e[128];
+  __shared__ double cs_c[256], cs_s[256], cs_d[256];
+  __shared__ cd cs_e[256];
   __shared__ double red[JAC_THREADS / 32];
   __shared__ double floor_s;
   __shared__ int nrot;
@@ -82,7 +82,9 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
   }
   __syncthreads();
   bool conv = (np <= 1);
+  int sweeps_done = 0;
   for (int sweep = 0; sweep < MAX_SWEEPS && !conv; ++sweep) {
+    ++sweeps_done;
     if (tid == 0) nrot = 0;
     __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
@@ -94,7 +96,9 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
         double ab = sqrt(cabs2(apq));
         double c = 1.0, s = 0.0, dl = 0.0;
         cd e = mk(1.0, 0.0);
-        if (ab > floor_s && ab > 1e-15 * sqrt(fabs(app * aqq))) {
+        // rounding leaves off-diagonal noise ~ eps * max(|app|, |aqq|): rotating below
+        // that level cannot converge, and leaving it perturbs eigenvectors by ~1e-15
+        if (ab > floor_s && ab > 1e-15 * fmax(fabs(app), fabs(aqq))) {
           herm_rot(app, aqq, apq, c, s, e);
           dl = (s / c) * ab;        // app' = app - t|apq|, aqq' = aqq + t|apq|
           atomicAdd(&nrot, 1);
@@ -145,6 +149,7 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
     __syncthreads();
   }
   if (tid == 0 && status) status[b] = conv ? 0 : 1;
+  if (tid == 0 && sweeps_out) sweeps_out[b] = sweeps_done;
   for (int i = tid; i < n; i += blockDim.x) {
     double li = a[i * np + i].x;
     int rank = 0;
@@ -266,10 +271,103 @@ svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout
   }
 }
 
-cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV, cd* work,
-                         int* status, cudaStream_t st) {
+// W = L^{-H} with L L^H = G + shift * max_i G_ii * I (G Hermitian PSD, n x n).
+// One block per matrix: right-looking Cholesky, then forward substitution for
+// the columns of L^{-1} (one thread per column).  Used so that Y W has
+// orthonormal columns when G = Y^H Y; the shift keeps it well defined for
+// rank-deficient Y and damps directions below shift * max G_ii smoothly.
+template <typename C>
+__global__ void __launch_bounds__(JAC_THREADS)
+chol_w_kernel(const cd* Gin, int n, double shift, C* Wout, cd* work, int use_smem) {
+  extern __shared__ double4 smraw4[];
+  __shared__ double red[JAC_THREADS / 32];
+  __shared__ double sh_s;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  cd* L = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * 2 * n * n;
+  cd* X = L + (long long)n * n;
+  const cd* G = Gin + (long long)b * n * n;
+  double mx = 0.0;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    int i = idx / n, j = idx % n;
+    cd g = G[idx];
+    L[idx] = (j <= i) ? g : mk(0.0, 0.0);
+    if (i == j) mx = fmax(mx, g.x);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < JAC_THREADS / 32; ++w) m = fmax(m, red[w]);
+    sh_s = shift * m;
+  }
+  __syncthreads();
+  const double sft = sh_s;
+  C* W = Wout + (long long)b * n * n;
+  if (!(sft > 0.0)) {              // Y = 0: no directions
+    for (int idx = tid; idx < n * n; idx += blockDim.x) W[idx] = from_cd<C>(mk(0.0, 0.0));
+    return;
+  }
+  for (int i = tid; i < n; i += blockDim.x) L[i * n + i].x += sft;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      double d = L[j * n + j].x;
+      L[j * n + j] = mk(sqrt(d > sft * 1e-3 ? d : sft), 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / L[j * n + j].x;
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i * n + j] = cscale(L[i * n + j], inv);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {        // trailing lower triangle
+      int i = j + 1 + idx / m, k = j + 1 + idx % m;
+      if (k > i) continue;
+      L[i * n + k] = csub(L[i * n + k], cmul(L[i * n + j], cconj(L[k * n + j])));
+    }
+    __syncthreads();
+  }
+  // X = L^{-1}: column c by forward substitution (one thread per column)
+  for (int c = tid; c < n; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) X[i * n + c] = mk(0.0, 0.0);
+    for (int i = c; i < n; ++i) {
+      cd acc = mk(i == c ? 1.0 : 0.0, 0.0);
+      for (int k = c; k < i; ++k) acc = csub(acc, cmul(L[i * n + k], X[k * n + c]));
+      X[i * n + c] = cscale(acc, 1.0 / L[i * n + i].x);
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {          // W = X^H
+    int i = idx / n, j = idx % n;
+    W[idx] = from_cd<C>(cconj(X[j * n + i]));
+  }
+}
+
+cudaError_t chol_w_batched(const cd* G, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+                           cudaStream_t st) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
-  if (n > 256) return cudaErrorInvalidValue;  // round parameters held in 128-entry tables
+  size_t bytes = (size_t)2 * n * n * sizeof(cd);
+  int use_smem = bytes <= SMEM_LIMIT;
+  if (!use_smem && !work) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(chol_w_kernel<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    attr = true;
+  }
+  if (w_f64)
+    chol_w_kernel<cd><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(G, n, shift, (cd*)W, work, use_smem);
+  else
+    chol_w_kernel<cf><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(G, n, shift, (cf*)W, work, use_smem);
+  return cudaGetLastError();
+}
+
+bool chol_fits_smem(int n) { return (size_t)2 * n * n * sizeof(cd) <= SMEM_LIMIT; }
+
+cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV, cd* work,
+                         int* status, cudaStream_t st, int* sweeps_out) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  if (n > 512) return cudaErrorInvalidValue;  // round parameters held in 256-entry tables
   int np = n + (n & 1);
   size_t bytes = (size_t)2 * np * np * sizeof(cd);
   int use_smem = bytes <= SMEM_LIMIT;
@@ -279,7 +377,8 @@ cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double*
     cudaFuncSetAttribute(eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
     attr = true;
   }
-  eigh_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status, use_smem);
+  eigh_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status, use_smem,
+                                                                sweeps_out);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,17 @@ namespace tns {
 //   work: >= batch * 2 * np * np complex (np = n rounded up to even), used when the
 //         matrix does not fit in shared memory; may be null otherwise
 //   status: [batch] 0 = converged, 1 = sweep cap reached (result still returned)
+//   sweeps_out: optional [batch] number of sweeps used.  n <= 512.
 cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV,
-                         cd* work, int* status, cudaStream_t st);
+                         cd* work, int* status, cudaStream_t st, int* sweeps_out = nullptr);
+
+// Orthonormalising map from a Gram matrix: W = L^{-H} with
+// L L^H = G + shift * max_i G_ii * I, batched n x n (contiguous); W written as
+// complex128 (w_f64) or complex64.  work: >= batch * 2 n^2 complex when
+// !chol_fits_smem(n).
+cudaError_t chol_w_batched(const cd* G, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+                           cudaStream_t st);
+bool chol_fits_smem(int n);
 
 // Thin SVD A = U diag(sigma) V^H of a batch of m x n matrices with m >= n by
 // one-sided (Hestenes) Jacobi.  A (row-major, lda, batch stride sA) is destroyed.

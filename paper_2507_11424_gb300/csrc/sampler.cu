@@ -21,6 +21,9 @@
 
 namespace tns {
 
+static constexpr double ORTH_SHIFT_FP64 = 1e-14;
+static constexpr double ORTH_SHIFT_MIXED = 1e-8;
+
 static inline int nblk(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 1 << 20); }
 
 // ------------------------------------------------------------------ kernels
@@ -46,20 +49,6 @@ __global__ void omega_kernel(C* out, int n, int kk, uint64_t seed, int stage, in
                               (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
     double re = 2.0 * u53(w.v[0], w.v[1]) - 1.0, im = 2.0 * u53(w.v[2], w.v[3]) - 1.0;
     out[idx] = from_cd<C>(mk(re, im));
-  }
-}
-
-// W = V diag(lam^{-1/2}) over eigenvalues > cut * lam_max, batched; converted to C.
-template <typename C>
-__global__ void gram_w_batched_kernel(const double* lam, const cd* V, int n, double cut, C* Wm, int batch) {
-  long long tot = (long long)batch * n * n;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long b = idx / ((long long)n * n);
-    int c = (int)(idx % n);
-    double l = lam[b * n + c], lmax = lam[b * n];
-    double f = (lmax > 0.0 && l > cut * lmax) ? 1.0 / sqrt(l) : 0.0;
-    Wm[idx] = from_cd<C>(cscale(V[idx], f));
   }
 }
 
@@ -243,6 +232,24 @@ __global__ void amp_final_kernel(const C* const* sites, int W, long long S, doub
 }
 
 // ------------------------------------------------------------------ host side
+enum ProfClass { PC_ENV = 0, PC_SWEEP = 1, PC_ZIP = 2, PC_EIGH = 3, PC_MARG = 4 };
+
+// contract() bracketed by the state's profiler (no-op when profiling is off).
+static cudaError_t pcontract(tns_state* s, int cls, const TView& A, const TView& B, const TView& C, Prec p) {
+  cudaEvent_t ev = s->prof.begin(s->st);
+  double fl = 0.0;
+  cudaError_t e = contract(A, B, C, p, s->st, make_double2(1.0, 0.0), make_double2(0.0, 0.0), &fl);
+  s->prof.end(cls, ev, fl, s->st);
+  return e;
+}
+
+static cudaError_t peigh(tns_state* s, cd* A, int n, int batch, double* lam, cd* V, cd* work, int* status) {
+  cudaEvent_t ev = s->prof.begin(s->st);
+  cudaError_t e = eigh_batched(A, (long long)n * n, n, n, batch, lam, V, (long long)n * n, work, status, s->st);
+  s->prof.end(PC_EIGH, ev, 0.0, s->st);
+  return e;
+}
+
 struct Ctx {
   tns_state* s;
   cudaStream_t st;
@@ -251,6 +258,10 @@ struct Ctx {
   size_t esz;
   uint64_t seed;
   int R;
+  // Shift of the Cholesky orthonormalisation, relative to max_i G_ii: 1e-14 in FP64
+  // (100x the rounding floor of an FP64 Gram); 1e-8 in the mixed path, where the
+  // FP32 product Y W amplifies rounding by (shift)^{-1/2} ~ 1e4.
+  double orth_shift;
 };
 
 template <typename F> static void dispatch(bool f64, F&& f) {
@@ -351,34 +362,31 @@ static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
   return TNS_OK;
 }
 
-// Orthonormalising map W (kk x kk) with Y W orthonormal, from the Gram matrix (FP64 eigh).
+// Orthonormalising map W (kk x kk): Y W has orthonormal columns, from the Gram
+// matrix G = Y^H Y (FP64) by a shifted Cholesky factorisation
+// L L^H = G + orth_shift * max_i G_ii * I, W = L^{-H}.
 static tns_status orth_w(Ctx& cx, void* Y, long long S, long long M, int kk, void* Wout) {
   tns_state* s = cx.s;
-  cd *G, *V;
-  double* lam;
-  int* status;
+  cd* G;
   TNS_TRY(wsget(s, "z_G", sizeof(cd) * S * kk * kk, (void**)&G));
-  TNS_TRY(wsget(s, "z_V", sizeof(cd) * S * kk * kk, (void**)&V));
-  TNS_TRY(wsget(s, "z_lam", sizeof(double) * S * kk, (void**)&lam));
-  TNS_TRY(wsget(s, "z_status", sizeof(int) * S, (void**)&status));
-  TNS_TRY_CUDA(contract(view(Y, "Smc", {S, M, kk}, true), view(Y, "Sme", {S, M, kk}), view(G, "Sce", {S, kk, kk}),
-                        cx.gram, cx.st));
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Y, "Smc", {S, M, kk}, true), view(Y, "Sme", {S, M, kk}),
+                         view(G, "Sce", {S, kk, kk}), cx.gram));
   cd* work = nullptr;
-  if (!jacobi_fits_smem(kk, kk)) {
-    long long np = kk + (kk & 1);
-    TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
-  }
-  TNS_TRY_CUDA(eigh_batched(G, (long long)kk * kk, kk, kk, (int)S, lam, V, (long long)kk * kk, work, status, cx.st));
-  dispatch(cx.f64, [&](auto* tp) {
-    using C = std::remove_pointer_t<decltype(tp)>;
-    gram_w_batched_kernel<C><<<nblk(S * kk * kk), 256, 0, cx.st>>>(lam, V, kk, 1e-12, (C*)Wout, (int)S);
-  });
-  s->launches += 2;
+  if (!chol_fits_smem(kk)) TNS_TRY(wsget(s, "z_cwork", sizeof(cd) * S * 2 * kk * kk, (void**)&work));
+  cudaEvent_t ev = s->prof.begin(cx.st);
+  TNS_TRY_CUDA(chol_w_batched(G, kk, (int)S, cx.orth_shift, Wout, cx.f64, work, cx.st));
+  s->prof.end(PC_EIGH, ev, 0.0, cx.st);
+  s->launches++;
   return TNS_OK;
 }
 
-// Rank-R factorisation T = K C of each batch entry (T: S x M x N).  K has
-// orthonormal columns with the phase convention; C = K^H T.
+// Rank-R factorisation T = K C of each batch entry (T: S x M x N): randomized
+// range finder with one subspace iteration, orthonormalising after every
+// application (Halko, Martinsson, Tropp 2011, Alg. 4.4):
+//   Y0 = T Omega, Q0 = orth(Y0), Z = orth(T^H Q0), Y = T Z, Q = orth(Y),
+// then the truncated SVD of B = Q^H T from the FP64 eigendecomposition of B B^H:
+//   K = Q U_B[:, :R] (column phases fixed), C = K^H T.
+// With k = R + 8 >= N the test matrix is the identity and Y = T.
 static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long N, int stage, int row, int site,
                            void* Kout, void* Cout, int* Rk_out) {
   tns_state* s = cx.s;
@@ -402,21 +410,24 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
       omega_kernel<C><<<nblk(N * kk), 256, 0, cx.st>>>((C*)om, (int)N, kk, cx.seed, stage, row, site);
     });
     s->launches++;
-    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}), cx.gp, cx.st));
-    // one subspace iteration: Y <- T T^H orth(Y)
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}),
+                           cx.gp));
     TNS_TRY(orth_w(cx, Y, S, M, kk, Wm));
-    TNS_TRY_CUDA(contract(view(Y, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}), view(Q, "Sme", {S, M, kk}), cx.gp,
-                          cx.st));
-    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}, true), view(Q, "Sme", {S, M, kk}), view(Z, "Sne", {S, N, kk}),
-                          cx.gp, cx.st));
-    TNS_TRY_CUDA(contract(view(T, "Smn", {S, M, N}), view(Z, "Sne", {S, N, kk}), view(Y, "Sme", {S, M, kk}), cx.gp,
-                          cx.st));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Y, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
+                           view(Q, "Sme", {S, M, kk}), cx.gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}, true), view(Q, "Sme", {S, M, kk}),
+                           view(Z, "Sne", {S, N, kk}), cx.gp));
+    TNS_TRY(orth_w(cx, Z, S, N, kk, Wm));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Z, "Snc", {S, N, kk}), view(Wm, "Sce", {S, kk, kk}),
+                           view(B, "Sne", {S, N, kk}), cx.gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(B, "Sne", {S, N, kk}),
+                           view(Y, "Sme", {S, M, kk}), cx.gp));
   }
   TNS_TRY(orth_w(cx, Ymat, S, M, kk, Wm));
-  TNS_TRY_CUDA(contract(view(Ymat, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}), view(Q, "Sme", {S, M, kk}),
-                        cx.gp, cx.st));
-  TNS_TRY_CUDA(contract(view(Q, "Sme", {S, M, kk}, true), view(T, "Smn", {S, M, N}), view(B, "Sen", {S, kk, N}),
-                        cx.gp, cx.st));
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Ymat, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
+                         view(Q, "Sme", {S, M, kk}), cx.gp));
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Q, "Sme", {S, M, kk}, true), view(T, "Smn", {S, M, N}),
+                         view(B, "Sen", {S, kk, N}), cx.gp));
   cd *Hm, *V;
   double* mu;
   int* status;
@@ -424,27 +435,27 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   TNS_TRY(wsget(s, "z_V2", sizeof(cd) * S * kk * kk, (void**)&V));
   TNS_TRY(wsget(s, "z_mu", sizeof(double) * S * kk, (void**)&mu));
   TNS_TRY(wsget(s, "z_status2", sizeof(int) * S, (void**)&status));
-  TNS_TRY_CUDA(contract(view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true), view(Hm, "Sef", {S, kk, kk}),
-                        cx.gram, cx.st));
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
+                         view(Hm, "Sef", {S, kk, kk}), cx.gram));
   cd* work = nullptr;
   if (!jacobi_fits_smem(kk, kk)) {
     long long np = kk + (kk & 1);
     TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
   }
-  TNS_TRY_CUDA(eigh_batched(Hm, (long long)kk * kk, kk, kk, (int)S, mu, V, (long long)kk * kk, work, status, cx.st));
+  TNS_TRY_CUDA(peigh(s, Hm, kk, (int)S, mu, V, work, status));
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     take_cols_kernel<C><<<nblk(S * kk * Rk), 256, 0, cx.st>>>(V, kk, Rk, (C*)UBt, (int)S);
   });
-  TNS_TRY_CUDA(contract(view(Q, "Sme", {S, M, kk}), view(UBt, "Ser", {S, kk, Rk}), view(Kout, "Smr", {S, M, Rk}),
-                        cx.gp, cx.st));
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Q, "Sme", {S, M, kk}), view(UBt, "Ser", {S, kk, Rk}),
+                         view(Kout, "Smr", {S, M, Rk}), cx.gp));
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     phase_fix_kernel<C><<<dim3(Rk, (unsigned)S), 128, 0, cx.st>>>((C*)Kout, (int)M, Rk);
   });
-  TNS_TRY_CUDA(contract(view(Kout, "Smr", {S, M, Rk}, true), view(T, "Smn", {S, M, N}), view(Cout, "Srn", {S, Rk, N}),
-                        cx.gp, cx.st));
-  s->launches += 3;
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Kout, "Smr", {S, M, Rk}, true), view(T, "Smn", {S, M, N}),
+                         view(Cout, "Srn", {S, Rk, N}), cx.gp));
+  s->launches += 2;
   return TNS_OK;
 }
 
@@ -495,7 +506,7 @@ static tns_status zip(Ctx& cx, ZipSpec& zs) {
     xd.push_back(bdm);
     xsz *= bdm;
     TNS_TRY(wsget(s, "zip_X", cx.esz * S * xsz, &X));
-    TNS_TRY_CUDA(contract(view(Cp, "Skal", {S, kprev, a, l}), mv, view(X, xl, xd), cx.gp, cx.st));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Cp, "Skal", {S, kprev, a, l}), mv, view(X, xl, xd), cx.gp));
     // T[S][k][out][b][r] = sum_{l, Pc} X w
     std::vector<long long> td = {S, kprev};
     std::string tl = "Sk";
@@ -514,7 +525,7 @@ static tns_status zip(Ctx& cx, ZipSpec& zs) {
     td.push_back(r);
     const long long Ncol = bdm * r;
     TNS_TRY(wsget(s, "zip_T", cx.esz * S * Mrow * Ncol, &T));
-    TNS_TRY_CUDA(contract(view(X, xl, xd), wv, view(T, tl, td), cx.gp, cx.st));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(X, xl, xd), wv, view(T, tl, td), cx.gp));
     out.phys[j] = pdims;
     if (j == W - 1) {
       if (Ncol != 1) { set_error("zip: open right bond at the last site"); return TNS_ERR_STATE; }
@@ -655,6 +666,7 @@ static tns_status make_ctx(tns_state* s, int chi_b, uint64_t seed, Ctx& cx) {
   cx.esz = cx.f64 ? sizeof(cd) : sizeof(cf);
   cx.seed = seed;
   cx.R = chi_b;
+  cx.orth_shift = cx.f64 ? ORTH_SHIFT_FP64 : ORTH_SHIFT_MIXED;
   return ensure_work_cells(s, cx.f64);
 }
 
@@ -793,14 +805,14 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         // R1: T1[S][a][s][B][d][f] = sum_A K'[a,s,d,A] F_{j+1}[A,f,B]
         TView Fv = view(Fs[j + 1], "SAfB", {Sz, kb, rf, kb});
         if (j + 1 == W) Fv.stride[0] = 0;
-        TNS_TRY_CUDA(contract(Kview(j, 'a', 's', 'd', 'A', Sz, false), Fv,
-                              view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, Kview(j, 'a', 's', 'd', 'A', Sz, false), Fv,
+                              view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), cx.gp));
         // R2: T2[S][a][s][B][e][D] = sum_{d,f} T1 E[e,d,D,f]
-        TNS_TRY_CUDA(contract(view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
-                              view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
+                              view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp));
         // R3: F_j[S][a][e][c] = sum_{s,D,B} T2 conj K'[c,s,D,B]
-        TNS_TRY_CUDA(contract(view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
-                              view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
+                              view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp));
         dispatch(cx.f64, [&](auto* tp) {
           using C = std::remove_pointer_t<decltype(tp)>;
           normalize_kernel<C><<<(unsigned)Sz, 256, 0, cx.st>>>((C*)Fs[j], ka * re * ka);
@@ -825,25 +837,27 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         TView Ev = Eview(j);
         const long long re = vdim(Ev, 'e'), rf = vdim(Ev, 'f');
         // L1: U1[S][c][s][A][e][d] = sum_a L[a,e,c] K'[a,s,d,A]
-        TNS_TRY_CUDA(contract(view(Lc, "Saec", {S, ka, re, ka}), Kview(j, 'a', 's', 'd', 'A', S, false),
-                              view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(Lc, "Saec", {S, ka, re, ka}), Kview(j, 'a', 's', 'd', 'A', S, false),
+                              view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), cx.gp));
         // L2: U2[S][c][s][A][D][f] = sum_{e,d} U1 E[e,d,D,f]
-        TNS_TRY_CUDA(contract(view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
-                              view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
+                              view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp));
         // L3: G[S][s][A][f][B] = sum_{c,D} U2 conj K'[c,s,D,B]
-        TNS_TRY_CUDA(contract(view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), Kview(j, 'c', 's', 'D', 'B', S, true),
-                              view(Gb, "SsAfB", {S, P, kb, rf, kb}), cx.gp, cx.st));
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), Kview(j, 'c', 's', 'D', 'B', S, true),
+                              view(Gb, "SsAfB", {S, P, kb, rf, kb}), cx.gp));
         const int c = rev ? W - 1 - j : j;
         const int q = s->cell[s->cidx(b, c)].qubit;
         const long long nel = kb * rf * kb;
         const long long fst = (j + 1 == W || shared) ? 0 : kb * rf * kb;
         const long long kst = shared ? 0 : ka * P * Dd * kb;
+        cudaEvent_t mev = s->prof.begin(cx.st);
         dispatch(cx.f64, [&](auto* tp) {
           using C = std::remove_pointer_t<decltype(tp)>;
           marginal_kernel<C><<<(unsigned)S, 256, 0, cx.st>>>(
               (const C*)Gb, (int)P, nel, (const C*)Fs[j + 1], fst, (const C*)Kp.site[j], kst, (int)ka, (int)Dd,
               (int)kb, (C*)Ln, (C*)mnext.site[j], bits, forced, s->n, q < 0 ? 0 : q, logq, cond, cx.seed, s0);
         });
+        s->prof.end(PC_MARG, mev, 0.0, cx.st);
         s->launches++;
         mnext.phys[j] = {Dd};
         std::swap(Lc, Ln);
@@ -853,6 +867,7 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
     }
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  s->prof.resolve();
   return TNS_OK;
 }
 

@@ -18,8 +18,9 @@ struct Cell {
   int qubit = -1;            // -1: empty cell (physical dimension 1)
   int dim[5] = {1, 1, 1, 1, 1};
   bool edge[5] = {false, false, false, false, false};
-  cd* t = nullptr;           // device, capacity cap complex elements
+  cd* t = nullptr;           // device, capacity cap complex elements (inside the cell arena)
   long long cap = 0;
+  long long off = 0;         // element offset of t in the cell arena
   long long size() const { return (long long)dim[0] * dim[1] * dim[2] * dim[3] * dim[4]; }
 };
 
@@ -38,6 +39,21 @@ struct StoredMPS {
   std::vector<long long> bond;          // W+1 bond dims in logical order
   std::vector<std::vector<long long>> phys;  // per site physical dims (in stored order)
   bool reversed = false;
+};
+
+// Event-bracketed timing of kernel classes (see tns_profile_enable).
+struct Profiler {
+  static constexpr int NCLASS = 5;
+  bool on = false;
+  struct Rec { int cls; cudaEvent_t a, b; double flops; };
+  std::vector<Rec> pending;
+  double ms[NCLASS] = {0, 0, 0, 0, 0};
+  double flops[NCLASS] = {0, 0, 0, 0, 0};
+  long long n[NCLASS] = {0, 0, 0, 0, 0};
+  cudaEvent_t begin(cudaStream_t st);
+  void end(int cls, cudaEvent_t a, double fl, cudaStream_t st);
+  void resolve();   // after the stream is synchronised
+  void clear();
 };
 
 struct EnvCache {
@@ -62,11 +78,15 @@ struct tns_state {
   std::vector<int> qcell;               // qubit -> cell index
   std::vector<cd*> msg;                 // (cell*5 + leg): message into cell across leg, chi_max^2 capacity
   std::vector<cd*> msg_new;
+  cd* cell_arena = nullptr;             // every cell tensor, cell ci at cell[ci].off
+  cd* msg_arena = nullptr;              // message slot (cell*5 + leg) at slot * chi_max^2
+  cd* msg_new_arena = nullptr;
   double log_f = 0.0;
   long long version = 0;                // bumped whenever site tensors change
   long long launches = 0;
   tns::Workspace ws;
   tns::EnvCache env;
+  tns::Profiler prof;
   std::vector<void*> work_cells;        // working-precision copies of the cell tensors
   int work_prec = -1;
   long long work_version = -1;

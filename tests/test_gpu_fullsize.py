@@ -1,0 +1,48 @@
+"""Full-size parity on the benchmark workload (GPU, several minutes).
+
+10x10 square lattice, domain-wall Heisenberg quench, 7 layers, dt = 0.2,
+chi = 16, boundary rank chi_b = 64: the state is built by the library, written
+as a fixture, and the CPU oracle replays the conditionals q(x_v = 0 | prefix)
+along bitstrings the library drew, one sample per precision path.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import bmps, fixture
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def state(tmp_path_factory):
+    import paper_2507_11424_gb300 as pkg
+    from paper_2507_11424_gb300 import build
+    build.build()
+    cfg = w.CONFIGS["sq10x10"]
+    lat = w.make_lattice(cfg["lattice"])
+    bits = w.domain_wall_bits(lat)
+    st = pkg.TNSState(lat.grid_rc, lat.edges, bits, chi_max=cfg["chi"], prec="mixed")
+    for g in w.heisenberg_circuit(lat, cfg["layers"], cfg["dt"]):
+        st.apply_gate_layer(g, chi=cfg["chi"])
+        st.bp_gauge(300, 1e-10)
+    path = str(tmp_path_factory.mktemp("cfg2") / "cfg2.tnsf")
+    st.save(path)
+    return st, fixture.load(path), cfg, bits
+
+
+@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT_MIXED, 1e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
+def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
+    st, t, cfg, bits = state
+    R = cfg["chi_b"]
+    st.set_precision(prec)
+    n = 8 if prec == "mixed" else 1
+    xs, logq, cond = st.sample(R, n, seed=20250711, cond=True)
+    xs, logq, cond = xs.cpu().numpy(), logq.cpu().numpy(), cond.cpu().numpy()
+    assert np.isfinite(logq).all()
+    assert (xs.sum(axis=1) == bits.sum()).mean() >= 0.5          # U(1) sector mostly kept at chi_b = 64
+    E, _ = bmps.norm_envs(t, R, gram_cut=shift)
+    _, lq_o, q0_o = bmps.sample(t, R, 0, 20250711, forced=xs[:1], env=E, gram_cut=shift)
+    err = np.abs(cond[:1] - q0_o).max()
+    assert err < tol, f"max |q_gpu - q_oracle| = {err:.3e}"
+    assert abs(logq[0] - lq_o[0]) < 50 * tol
