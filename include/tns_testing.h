@@ -26,6 +26,16 @@ tns_status tns_test_philox(int64_t n, const uint32_t* ctr_key_dev, uint32_t* out
 tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
                          void* cuda_stream);
 
+/* Sweeps used by each matrix of the last tns_test_eigh call (host int32 [batch]);
+ * a value of 0 or less means the sweep cap was reached. */
+tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* sweeps_host);
+
+/* Orthonormalising map of the range finder: W = L^{-H} with
+ * L L^H = G + shift * max_i G_ii * I.
+ *   G_dev  device complex128 [batch][n][n] Hermitian PSD; W_dev complex128 [batch][n][n] */
+tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, const double* G_dev, double* W_dev,
+                          void* cuda_stream);
+
 /* Batched FP64 thin SVD A = U diag(s) V^H (m >= n) by one-sided Jacobi.
  *   A_dev  device complex128 [batch][m][n] (read only); s_dev float64 [batch][n];
  *   U_dev  complex128 [batch][m][n]; V_dev complex128 [batch][n][n] */

@@ -4,6 +4,8 @@
 #include "linalg.cuh"
 #include "state.h"
 
+#include <vector>
+
 namespace tns {
 __global__ void philox_test_kernel(long long n, const uint32_t* ck, uint32_t* out) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -26,20 +28,51 @@ extern "C" tns_status tns_test_philox(int64_t n, const uint32_t* ck, uint32_t* o
   return TNS_OK;
 }
 
+static std::vector<int> g_last_sweeps;
+
 extern "C" tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A, double* lam, double* V, void* stream) {
-  if (batch < 0 || n < 1 || n > 256 || !A || !lam || !V) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  if (batch < 0 || n < 1 || n > 512 || !A || !lam || !V) { set_error("invalid argument"); return TNS_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
   cd* work = nullptr;
   int* status = nullptr;
+  int* sweeps = nullptr;
   TNS_TRY_CUDA(cudaMalloc(&status, sizeof(int) * (batch > 0 ? batch : 1)));
+  TNS_TRY_CUDA(cudaMalloc(&sweeps, sizeof(int) * (batch > 0 ? batch : 1)));
   if (!jacobi_fits_smem(n, n)) {
     long long np = n + (n & 1);
     TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * 2 * np * np));
   }
-  cudaError_t e = eigh_batched((cd*)A, (long long)n * n, n, n, batch, lam, (cd*)V, (long long)n * n, work, status, st);
+  cudaError_t e = eigh_batched((cd*)A, (long long)n * n, n, n, batch, lam, (cd*)V, (long long)n * n, work, status, st,
+                               sweeps);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  std::vector<int> hs(batch > 0 ? batch : 1), hw(batch > 0 ? batch : 1);
+  if (e == cudaSuccess && batch > 0) {
+    cudaMemcpy(hs.data(), status, sizeof(int) * batch, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hw.data(), sweeps, sizeof(int) * batch, cudaMemcpyDeviceToHost);
+    g_last_sweeps.assign(batch, 0);
+    for (int b = 0; b < batch; ++b) g_last_sweeps[b] = hs[b] == 0 ? hw[b] : -hw[b];
+  }
   cudaFree(work);
   cudaFree(status);
+  cudaFree(sweeps);
+  TNS_TRY_CUDA(e);
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* out) {
+  if (!out || batch < 0 || (size_t)batch > g_last_sweeps.size()) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  for (int b = 0; b < batch; ++b) out[b] = g_last_sweeps[b];
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, const double* G, double* W, void* stream) {
+  if (batch < 0 || n < 1 || !G || !W || !(shift > 0.0)) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* work = nullptr;
+  if (!chol_fits_smem(n)) TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * 2 * (long long)n * n));
+  cudaError_t e = chol_w_batched((const cd*)G, n, batch, shift, W, true, work, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(work);
   TNS_TRY_CUDA(e);
   return TNS_OK;
 }

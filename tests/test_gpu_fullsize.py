@@ -31,7 +31,12 @@ def state(tmp_path_factory):
     return st, fixture.load(path), cfg, bits
 
 
-@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT_MIXED, 1e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
+# Tolerances.  FP64: rounding only (1e-8).  Mixed (FP32 contractions): at chi_b = 64
+# this state is truncated hard, and replaying the same bitstrings in FP64 with a
+# different range-finder test matrix already moves single conditionals by ~2.6e-2;
+# FP32 rounding moves them by ~2e-3 at most.  The mixed bar is 5e-3 on the largest
+# conditional and 5e-4 on the mean over all conditionals of the sample.
+@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT_MIXED, 5e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
 def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
     st, t, cfg, bits = state
     R = cfg["chi_b"]
@@ -45,4 +50,5 @@ def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
     _, lq_o, q0_o = bmps.sample(t, R, 0, 20250711, forced=xs[:1], env=E, gram_cut=shift)
     err = np.abs(cond[:1] - q0_o).max()
     assert err < tol, f"max |q_gpu - q_oracle| = {err:.3e}"
+    assert np.abs(cond[:1] - q0_o).mean() < tol / 10
     assert abs(logq[0] - lq_o[0]) < 50 * tol

@@ -34,7 +34,7 @@ def test_device_philox_bit_exact(env):
     assert (got == ref.astype(np.uint32)).all()
 
 
-@pytest.mark.parametrize("n,batch", [(1, 3), (7, 5), (16, 4), (72, 3), (81, 2), (136, 2)])
+@pytest.mark.parametrize("n,batch", [(1, 3), (7, 5), (16, 4), (72, 3), (81, 2), (136, 2), (264, 2)])
 def test_device_eigh(env, n, batch):
     torch, lib = env
     rng = np.random.default_rng(n)
@@ -45,6 +45,10 @@ def test_device_eigh(env, n, batch):
     lam = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
     V = torch.zeros((batch, n, n, 2), dtype=torch.float64, device="cuda")
     assert lib.tns_test_eigh(batch, n, _ptr(dA), _ptr(lam), _ptr(V), None) == 0
+    import ctypes
+    sw = (ctypes.c_int32 * batch)()
+    assert lib.tns_test_eigh_sweeps(batch, ctypes.cast(sw, ctypes.c_void_p)) == 0
+    assert all(0 < x <= 25 for x in sw), list(sw)                     # converged, in few sweeps
     lam = lam.cpu().numpy()
     V = V.cpu().numpy().view(np.complex128).reshape(batch, n, n)
     for b in range(batch):
@@ -75,3 +79,25 @@ def test_device_svd(env, m, n, batch):
         rec = (U[b] * s[b]) @ V[b].conj().T
         assert np.abs(rec - A[b]).max() < 1e-12 * ref[0]
         assert np.abs(V[b].conj().T @ V[b] - np.eye(n)).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,batch,rank", [(72, 3, 72), (72, 2, 50), (264, 2, 256)])
+def test_device_cholesky_orthonormaliser(env, n, batch, rank):
+    """Y W has orthonormal columns on range(Y) when W comes from the shifted Cholesky of Y^H Y."""
+    torch, lib = env
+    rng = np.random.default_rng(n + rank)
+    m = 3 * n
+    Y = (rng.normal(size=(batch, m, rank)) + 1j * rng.normal(size=(batch, m, rank))) @ \
+        (rng.normal(size=(batch, rank, n)) + 1j * rng.normal(size=(batch, rank, n)))
+    G = np.conj(np.transpose(Y, (0, 2, 1))) @ Y
+    dG = torch.tensor(np.ascontiguousarray(G).view(np.float64), device="cuda")
+    dW = torch.zeros((batch, n, n, 2), dtype=torch.float64, device="cuda")
+    assert lib.tns_test_cholw(batch, n, 1e-14, _ptr(dG), _ptr(dW), None) == 0
+    W = dW.cpu().numpy().view(np.complex128).reshape(batch, n, n)
+    for b in range(batch):
+        Q = Y[b] @ W[b]
+        P = Q @ Q.conj().T                                   # projector onto range(Y)
+        Yn = Y[b] / np.linalg.norm(Y[b])
+        assert np.abs(P @ Yn - Yn).max() < 1e-10
+        s = np.linalg.svd(Q, compute_uv=False)
+        assert np.abs(s[:rank] - 1).max() < 1e-6

@@ -196,11 +196,10 @@ def test_log_norm_matches_oracle(pkg, tmp_path):
     bits = w.domain_wall_bits(lat)
     st, _ = gpu_state(pkg, lat, bits, w.heisenberg_circuit(lat, 4, 0.2), 4)
     t = to_oracle(st, tmp_path)
-    for R in (4, 16, 64):
+    # (R = 256 still truncates here: the exact boundary rank at row 1 is up to 16^3)
+    for R in (4, 16, 64, 256):
         _, ln_o = bmps.norm_envs(t, R)
         assert abs(st.log_norm(R) - ln_o) < 1e-9
-    # exact limit equals the brute-force norm
-    assert abs(np.exp(st.log_norm(256)) - np.sum(np.abs(t.statevector_bruteforce()) ** 2)) < 1e-10
 
 
 def test_heavy_hex_cells_and_edge_cases(pkg, tmp_path):
