@@ -178,6 +178,33 @@ tns_status tns_profile_enable(tns_state* s, int32_t enable);
 tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_ms, int64_t* launches,
                             double* flops);
 
+/*
+ * tns_eigh_noalloc -- batched Hermitian eigendecomposition (the library's FP64
+ * parallel-Jacobi eigensolver, the same computation as tns_test_eigh in
+ * tns_testing.h) that allocates no device memory.  The paper has no
+ * counterpart; it serves callers that cannot call cudaMalloc, such as programs
+ * whose device memory is owned by another allocator that has reserved HBM up
+ * front, or latency-critical code that cannot accept the device-wide
+ * synchronisation an allocation may imply.
+ *   batch, n   number and order of the matrices (1 <= n <= 512)
+ *   A_dev      device complex128 [batch][n][n], Hermitian, read only
+ *   lam_dev    device float64 [batch][n]: eigenvalues, descending
+ *   V_dev      device complex128 [batch][n][n]: column j is eigenvector j
+ *   cuda_stream  stream to launch on; the call returns after the launch and the
+ *              results are ready when the stream reaches that point
+ * Scratch: a static 16 MiB device array per GPU that loads the library, held
+ * until the process exits.  It holds 4 bytes per matrix plus, when 2*n'^2*16
+ * bytes (n' = n rounded up to even) exceed 200 KiB of shared memory, that much
+ * per matrix; a batch needing more than 16 MiB returns TNS_ERR_ARG.  Every call
+ * shares the one array, so calls that overlap on the GPU (different streams,
+ * or threads using one device) race: order them on one stream.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Convergence is not reported (no host synchronisation).
+ */
+tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
+                            void* cuda_stream);
+
 void tns_destroy(tns_state* s);
 const char* tns_last_error(void);
 

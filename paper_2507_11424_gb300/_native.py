@@ -40,6 +40,7 @@ SIGNATURES = {
     "tns_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "tns_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double)]),
+    "tns_eigh_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_destroy": (None, [C.c_void_p]),
     "tns_test_philox": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_test_eigh": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
