@@ -149,6 +149,13 @@ tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* log_norm);
 /* Select the precision of later tns_sample / tns_amplitude calls. */
 tns_status tns_set_precision(tns_state* s, tns_prec prec);
 
+/* Select how the mixed-precision path runs its environment contractions (the
+ * dominant GEMMs of the marginal sweeps): 1 (default) = tcgen05 tensor cores,
+ * kind::tf32 with a three-pass hi/lo split product (FP32-level accuracy);
+ * 0 = FP32 CUDA cores.  Shapes the tensor-core kernel does not support fall back
+ * to CUDA cores automatically. */
+tns_status tns_set_tensor_cores(tns_state* s, int32_t enable);
+
 /* Query: grid rows/cols after orientation, whether it was transposed, and the
  * current maximum bond dimension. */
 tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int32_t* transposed, int32_t* chi_now);
@@ -170,8 +177,9 @@ tns_status tns_launch_count(const tns_state* s, int64_t* launches);
  * complex multiply-add of the contraction as written, excluding any padding).
  * Classes: 0 = environment contractions (the row's norm-environment GEMMs of
  * the marginal sweeps), 1 = other marginal-sweep contractions, 2 = zip-up
- * compression contractions, 3 = FP64 Jacobi eigensolves, 4 = fused
- * marginal/draw/project kernel.  tns_profile_enable(s, 1) also clears the
+ * compression contractions, 3 = FP64 factorisations (Cholesky, Jacobi), 4 =
+ * fused marginal/draw/project kernel, 5 = tensor-core operand preparation
+ * (TF32 remainders and the real block expansion of the environments).  tns_profile_enable(s, 1) also clears the
  * counters.
  */
 tns_status tns_profile_enable(tns_state* s, int32_t enable);

@@ -36,6 +36,14 @@ tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* sweeps_host);
 tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, const double* G_dev, double* W_dev,
                           void* cuda_stream);
 
+/* Tensor-core complex GEMM used by the mixed-precision marginal sweeps:
+ * C = A B^T with A complex64 [M][K], B complex64 [N][K] (K contiguous), C complex64
+ * [M][N], computed by tcgen05 kind::tf32 with a three-pass hi/lo split.
+ * Returns TNS_ERR_STATE when the shape is not supported by the tensor-core path
+ * (K odd or below 16) and TNS_ERR_NUMERIC when a pipeline wait timed out. */
+tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const float* A_dev, const float* B_dev, float* C_dev,
+                           void* cuda_stream);
+
 /* Batched FP64 thin SVD A = U diag(s) V^H (m >= n) by one-sided Jacobi.
  *   A_dev  device complex128 [batch][m][n] (read only); s_dev float64 [batch][n];
  *   U_dev  complex128 [batch][m][n]; V_dev complex128 [batch][n][n] */

@@ -32,6 +32,7 @@ SIGNATURES = {
     "tns_log_fidelity": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "tns_log_norm": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
     "tns_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
+    "tns_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),
     "tns_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                             C.POINTER(C.c_int32)]),
     "tns_save": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -46,6 +47,7 @@ SIGNATURES = {
     "tns_test_eigh": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_test_eigh_sweeps": (C.c_int, [C.c_int32, C.c_void_p]),
     "tns_test_cholw": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tns_test_tcgemm": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_test_svd": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     "tns_last_error": (C.c_char_p, []),

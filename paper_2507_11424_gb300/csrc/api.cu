@@ -305,6 +305,12 @@ extern "C" tns_status tns_set_precision(tns_state* s, tns_prec prec) {
   return TNS_OK;
 }
 
+extern "C" tns_status tns_set_tensor_cores(tns_state* s, int32_t enable) {
+  if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
+  s->tensor_cores = enable != 0;
+  return TNS_OK;
+}
+
 extern "C" tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int32_t* transposed, int32_t* chi_now) {
   if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
   int chi = 1;

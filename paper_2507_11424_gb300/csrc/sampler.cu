@@ -18,6 +18,7 @@
 
 #include "linalg.cuh"
 #include "state.h"
+#include "tc_gemm.cuh"
 
 namespace tns {
 
@@ -232,7 +233,7 @@ __global__ void amp_final_kernel(const C* const* sites, int W, long long S, doub
 }
 
 // ------------------------------------------------------------------ host side
-enum ProfClass { PC_ENV = 0, PC_SWEEP = 1, PC_ZIP = 2, PC_EIGH = 3, PC_MARG = 4 };
+enum ProfClass { PC_ENV = 0, PC_SWEEP = 1, PC_ZIP = 2, PC_EIGH = 3, PC_MARG = 4, PC_PREP = 5 };
 
 // contract() bracketed by the state's profiler (no-op when profiling is off).
 static cudaError_t pcontract(tns_state* s, int cls, const TView& A, const TView& B, const TView& C, Prec p) {
@@ -263,6 +264,47 @@ struct Ctx {
   // FP32 product Y W amplifies rounding by (shift)^{-1/2} ~ 1e4.
   double orth_shift;
 };
+
+static long long label_stride(const TView& v, char l) {
+  for (size_t i = 0; i < v.labels.size(); ++i)
+    if (v.labels[i] == l) return v.stride[i];
+  return 0;
+}
+
+// Environment contraction C[M][(n1,n2)] = sum_{(k1,k2)} A[M][(k1,k2)] E[...] on the
+// tensor cores (mixed path): A contiguous M x K complex64, E read through the
+// labels (n1, n2, k1, k2).  Returns false when the shape is not supported.
+struct TcBufs {
+  float *Alo, *Bhi, *Blo;
+  int* err;
+};
+static bool tc_env(tns_state* s, cudaStream_t st, const TcBufs& tb, void* A, long long M, const TView& E, char n1,
+                   char n2, char k1, char k2, void* Cout, cudaError_t* e_out) {
+  long long dn1 = 1, dn2 = 1, dk1 = 1, dk2 = 1;
+  for (size_t i = 0; i < E.labels.size(); ++i) {
+    char c = E.labels[i];
+    if (c == n1) dn1 = E.dim[i];
+    if (c == n2) dn2 = E.dim[i];
+    if (c == k1) dk1 = E.dim[i];
+    if (c == k2) dk2 = E.dim[i];
+  }
+  const long long N = dn1 * dn2, K = dk1 * dk2;
+  const int Kr = (int)(2 * K), Nr = (int)(2 * N);
+  if (!tc_gemm_supported(M, Nr, Kr, Kr, Kr, Nr)) return false;
+  cudaEvent_t ev = s->prof.begin(st);
+  cudaError_t e = tf32_lo((const float*)A, tb.Alo, M * Kr, st);
+  if (e == cudaSuccess)
+    e = expand_b(E.ptr, (int)dn1, (int)dn2, label_stride(E, n1), label_stride(E, n2), (int)dk1, (int)dk2,
+                 label_stride(E, k1), label_stride(E, k2), tb.Bhi, tb.Blo, st);
+  s->prof.end(PC_PREP, ev, 0.0, st);
+  ev = s->prof.begin(st);
+  if (e == cudaSuccess) e = tc_gemm_tf32x3((const float*)A, tb.Alo, M, Kr, Kr, tb.Bhi, tb.Blo, Nr, Kr, (float*)Cout, Nr,
+                                           tb.err, st);
+  s->prof.end(PC_ENV, ev, 8.0 * (double)M * (double)N * (double)K, st);
+  s->launches += 3;
+  *e_out = e;
+  return true;
+}
 
 template <typename F> static void dispatch(bool f64, F&& f) {
   if (f64) f((cd*)nullptr);
@@ -749,6 +791,16 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   TNS_TRY(wsget(s, "s_G", cx.esz * chunk * 2 * F_cap, &Gb));
   TNS_TRY(wsget(s, "s_bigA", cx.esz * chunk * big_cap, &bigA));
   TNS_TRY(wsget(s, "s_bigB", cx.esz * chunk * big_cap, &bigB));
+  const bool use_tc = !cx.f64 && s->tensor_cores;
+  TcBufs tb{nullptr, nullptr, nullptr, nullptr};
+  if (use_tc) {
+    const long long kmax = R * chimax;                      // K, N <= R * chi
+    TNS_TRY(wsget(s, "s_tc_Alo", cx.esz * chunk * big_cap, (void**)&tb.Alo));
+    TNS_TRY(wsget(s, "s_tc_Bhi", sizeof(float) * 4 * kmax * kmax, (void**)&tb.Bhi));
+    TNS_TRY(wsget(s, "s_tc_Blo", sizeof(float) * 4 * kmax * kmax, (void**)&tb.Blo));
+    TNS_TRY(wsget(s, "s_tc_err", sizeof(int), (void**)&tb.err));
+    TNS_TRY_CUDA(cudaMemsetAsync(tb.err, 0, sizeof(int), cx.st));
+  }
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     fill_kernel<C><<<nblk(chunk), 256, 0, cx.st>>>((C*)ones, chunk, 1.0);
@@ -808,8 +860,11 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, Kview(j, 'a', 's', 'd', 'A', Sz, false), Fv,
                               view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), cx.gp));
         // R2: T2[S][a][s][B][e][D] = sum_{d,f} T1 E[e,d,D,f]
-        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
-                              view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp));
+        cudaError_t ge = cudaSuccess;
+        if (!(use_tc && tc_env(s, cx.st, tb, bigA, Sz * ka * P * kb, Ev, 'e', 'D', 'd', 'f', bigB, &ge)))
+          ge = pcontract(s, PC_ENV, view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
+                         view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp);
+        TNS_TRY_CUDA(ge);
         // R3: F_j[S][a][e][c] = sum_{s,D,B} T2 conj K'[c,s,D,B]
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
                               view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp));
@@ -840,8 +895,11 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(Lc, "Saec", {S, ka, re, ka}), Kview(j, 'a', 's', 'd', 'A', S, false),
                               view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), cx.gp));
         // L2: U2[S][c][s][A][D][f] = sum_{e,d} U1 E[e,d,D,f]
-        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
-                              view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp));
+        cudaError_t ge = cudaSuccess;
+        if (!(use_tc && tc_env(s, cx.st, tb, bigA, S * ka * P * kb, Ev, 'D', 'f', 'e', 'd', bigB, &ge)))
+          ge = pcontract(s, PC_ENV, view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
+                         view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp);
+        TNS_TRY_CUDA(ge);
         // L3: G[S][s][A][f][B] = sum_{c,D} U2 conj K'[c,s,D,B]
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), Kview(j, 'c', 's', 'D', 'B', S, true),
                               view(Gb, "SsAfB", {S, P, kb, rf, kb}), cx.gp));
@@ -868,6 +926,11 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
   s->prof.resolve();
+  if (use_tc) {
+    int herr = 0;
+    TNS_TRY_CUDA(cudaMemcpy(&herr, tb.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { set_error("tensor-core GEMM pipeline wait timed out"); return TNS_ERR_NUMERIC; }
+  }
   return TNS_OK;
 }
 

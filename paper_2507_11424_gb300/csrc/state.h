@@ -43,13 +43,13 @@ struct StoredMPS {
 
 // Event-bracketed timing of kernel classes (see tns_profile_enable).
 struct Profiler {
-  static constexpr int NCLASS = 5;
+  static constexpr int NCLASS = 6;
   bool on = false;
   struct Rec { int cls; cudaEvent_t a, b; double flops; };
   std::vector<Rec> pending;
-  double ms[NCLASS] = {0, 0, 0, 0, 0};
-  double flops[NCLASS] = {0, 0, 0, 0, 0};
-  long long n[NCLASS] = {0, 0, 0, 0, 0};
+  double ms[NCLASS] = {0, 0, 0, 0, 0, 0};
+  double flops[NCLASS] = {0, 0, 0, 0, 0, 0};
+  long long n[NCLASS] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t begin(cudaStream_t st);
   void end(int cls, cudaEvent_t a, double fl, cudaStream_t st);
   void resolve();   // after the stream is synchronised
@@ -89,6 +89,7 @@ struct tns_state {
   tns::Profiler prof;
   std::vector<void*> work_cells;        // working-precision copies of the cell tensors
   int work_prec = -1;
+  bool tensor_cores = true;             // mixed path: environment GEMMs on tcgen05
   long long work_version = -1;
 
   int cidx(int r, int c) const { return r * W + c; }

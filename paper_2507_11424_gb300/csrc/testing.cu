@@ -2,6 +2,7 @@
 // through the C ABI so they can be compared with the CPU oracle in isolation.
 #include "../../include/tns_testing.h"
 #include "linalg.cuh"
+#include "tc_gemm.cuh"
 #include "state.h"
 
 #include <vector>
@@ -94,5 +95,33 @@ extern "C" tns_status tns_test_svd(int32_t batch, int32_t m, int32_t n, const do
   cudaFree(work);
   cudaFree(status);
   TNS_TRY_CUDA(e);
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const float* A, const float* B, float* C,
+                                      void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int Kr = 2 * K, Nr = 2 * N;
+  if (!tc_gemm_supported(M, Nr, Kr, Kr, Kr, Nr)) { set_error("shape not supported by the tensor-core path"); return TNS_ERR_STATE; }
+  float *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;
+  int* err = nullptr;
+  TNS_TRY_CUDA(cudaMalloc(&Alo, sizeof(float) * M * Kr));
+  TNS_TRY_CUDA(cudaMalloc(&Bhi, sizeof(float) * (size_t)Nr * Kr));
+  TNS_TRY_CUDA(cudaMalloc(&Blo, sizeof(float) * (size_t)Nr * Kr));
+  TNS_TRY_CUDA(cudaMalloc(&err, sizeof(int)));
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  cudaError_t e = tf32_lo(A, Alo, M * Kr, st);
+  if (e == cudaSuccess) e = expand_b(B, N, 1, K, 0, K, 1, 1, 0, Bhi, Blo, st);
+  if (e == cudaSuccess) e = tc_gemm_tf32x3(A, Alo, M, Kr, Kr, Bhi, Blo, Nr, Kr, C, Nr, err, st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(Alo);
+  cudaFree(Bhi);
+  cudaFree(Blo);
+  cudaFree(err);
+  TNS_TRY_CUDA(e);
+  if (herr) { set_error("tensor-core GEMM pipeline wait timed out"); return TNS_ERR_NUMERIC; }
   return TNS_OK;
 }

@@ -101,3 +101,23 @@ def test_device_cholesky_orthonormaliser(env, n, batch, rank):
         assert np.abs(P @ Yn - Yn).max() < 1e-10
         s = np.linalg.svd(Q, compute_uv=False)
         assert np.abs(s[:rank] - 1).max() < 1e-6
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 16), (1000, 512, 512), (4096, 1024, 1024), (257, 130, 18), (8192, 96, 64)])
+def test_device_tensor_core_gemm(env, M, N, K):
+    """tcgen05 tf32x3 complex GEMM C = A B^T against complex128 numpy (FP32-level accuracy)."""
+    torch, lib = env
+    rng = np.random.default_rng(M + N + K)
+    A = (rng.normal(size=(M, K)) + 1j * rng.normal(size=(M, K))).astype(np.complex64)
+    B = (rng.normal(size=(N, K)) + 1j * rng.normal(size=(N, K))).astype(np.complex64)
+    dA = torch.tensor(A.view(np.float32), device="cuda")
+    dB = torch.tensor(B.view(np.float32), device="cuda")
+    dC = torch.full((M, 2 * N), np.nan, dtype=torch.float32, device="cuda")
+    rc = lib.tns_test_tcgemm(M, N, K, _ptr(dA), _ptr(dB), _ptr(dC), None)
+    assert rc == 0, lib.tns_last_error()
+    C = dC.cpu().numpy().view(np.complex64).astype(np.complex128)
+    ref = A.astype(np.complex128) @ B.astype(np.complex128).T
+    scale = np.abs(A).max() * np.abs(B).max() * np.sqrt(K)
+    err = np.abs(C - ref).max() / scale
+    # FP32 accumulation over 2K real products: ~ sqrt(2K) * 2^-23 of the scale
+    assert err < 2.5e-7 * np.sqrt(2 * K), err

@@ -133,14 +133,15 @@ def test_sampler_exact_when_R_large(pkg, shape, prec, tol):
     assert np.abs(logq - ref).max() < tol
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
-def test_sampler_matches_oracle_config1(pkg, tmp_path, prec, tol):
+@pytest.mark.parametrize("prec,tol,tc", [("fp64", 1e-9, False), ("mixed", 1e-4, False), ("mixed", 1e-4, True)])
+def test_sampler_matches_oracle_config1(pkg, tmp_path, prec, tol, tc):
     """Config 1 (4x4, L=4, chi=4, chi_b=16): conditionals along the GPU's draws equal the oracle's."""
     lat = w.square(4, 4)
     bits = w.domain_wall_bits(lat)
     st, _ = gpu_state(pkg, lat, bits, w.heisenberg_circuit(lat, 4, 0.2), 4)
     t = to_oracle(st, tmp_path)
     st.set_precision(prec)
+    st.set_tensor_cores(tc)
     seed, n = 20250711, 48
     xs, logq, cond = st.sample(chi_b=16, n=n, seed=seed, cond=True)
     xs, logq, cond = xs.cpu().numpy(), logq.cpu().numpy(), cond.cpu().numpy()
@@ -237,3 +238,23 @@ def test_save_load_roundtrip(pkg, tmp_path):
     st3.set_precision("fp64")
     c, lc = st3.sample(16, 8, 5)
     assert (a.cpu().numpy() == c.cpu().numpy()).all()
+
+
+def test_tensor_core_path_matches_cuda_cores(pkg, tmp_path):
+    """Mixed path with environment GEMMs on tcgen05 vs on CUDA cores, and vs the oracle (5x5, chi = 8)."""
+    lat = w.square(5, 5)
+    bits = w.domain_wall_bits(lat)
+    st, _ = gpu_state(pkg, lat, bits, w.heisenberg_circuit(lat, 3, 0.2), 8)
+    t = to_oracle(st, tmp_path)
+    st.set_precision("mixed")
+    R, seed, n = 32, 77, 16
+    st.profile(True)
+    st.set_tensor_cores(True)
+    xs, lq1, c1 = st.sample(R, n, seed, cond=True)
+    prof = st.profile_read()
+    assert prof["env_gemm"]["launches"] > 0 and prof["tc_prep"]["launches"] > 0   # tensor cores really ran
+    st.set_tensor_cores(False)
+    xs2, lq2, c2 = st.sample(R, n, seed, cond=True)
+    assert np.abs(c1.cpu().numpy() - c2.cpu().numpy()).max() < 1e-4
+    _, lq_o, q0_o = bmps.sample(t, R, 0, seed, forced=xs.cpu().numpy(), gram_cut=bmps.ORTH_SHIFT_MIXED)
+    assert np.abs(c1.cpu().numpy() - q0_o).max() < 1e-4
