@@ -126,7 +126,7 @@ def _oracle_sampler_worker(path, R, seed, budget, q):
     from oracle import bmps, fixture
     t = fixture.load(path)
     t0 = time.time()
-    E, _ = bmps.norm_envs(t, R, gram_cut=bmps.ORTH_SHIFT_MIXED)
+    E, _ = bmps.norm_envs(t, R, gram_cut=bmps.ORTH_SHIFT)
     env_s = time.time() - t0
     rows_done, t1 = 0, time.time()
     H = t.H
@@ -140,7 +140,7 @@ def _oracle_sampler_worker(path, R, seed, budget, q):
         from oracle import philox
         qubits = [int(t.cell_qubit[b, c]) for c in cells]
         uni = philox.draw_uniforms(seed, 0, np.array([max(x, 0) for x in qubits]))
-        _, _, _, m_next = bmps.sample_row(m, row, Eb, R, seed, b, uniforms=uni, gram_cut=bmps.ORTH_SHIFT_MIXED)
+        _, _, _, m_next = bmps.sample_row(m, row, Eb, R, seed, b, uniforms=uni, gram_cut=bmps.ORTH_SHIFT)
         m = bmps.mirror_mps(m_next)
         rows_done += 1
         if time.time() - t1 > budget:
@@ -320,7 +320,7 @@ def run_reference(args):
     for g in groups:
         t.apply_group(g, chi)
         t.bp(2, 1e-10)
-    E, _ = bmps.norm_envs(t, R, gram_cut=bmps.ORTH_SHIFT_MIXED)
+    E, _ = bmps.norm_envs(t, R, gram_cut=bmps.ORTH_SHIFT)
     H = t.H
     m = [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(t.W)]
     times = []
@@ -335,7 +335,7 @@ def run_reference(args):
         qubits = [int(t.cell_qubit[b, c]) for c in cells]
         uni = philox.draw_uniforms(7, k // H, np.array([max(x, 0) for x in qubits]))
         t0 = time.time()
-        _, _, _, m_next = bmps.sample_row(m, row, Eb, R, 7, b, uniforms=uni, gram_cut=bmps.ORTH_SHIFT_MIXED)
+        _, _, _, m_next = bmps.sample_row(m, row, Eb, R, 7, b, uniforms=uni, gram_cut=bmps.ORTH_SHIFT)
         times.append(time.time() - t0)
         m = bmps.mirror_mps(m_next)
     step = sum(times[args.warmup:]) / max(1, args.steps)

@@ -38,12 +38,9 @@ from . import philox
 OVERSAMPLE = 8
 POWER_ITERS = 1
 # Shift of the Cholesky orthonormalisation of a range-finder basis, relative to
-# the largest diagonal entry of its Gram matrix (FP64 algorithm).  The library's
-# mixed-precision path uses ORTH_SHIFT_MIXED; pass gram_cut=ORTH_SHIFT_MIXED to
-# replay it.
+# the largest diagonal entry of its Gram matrix: it only regularises
+# rank-deficient bases (orth(Y) is an orthonormal basis of range(Y)).
 ORTH_SHIFT = 1e-14
-ORTH_SHIFT_MIXED = 1e-8
-GRAM_CUT, GRAM_CUT_MIXED = ORTH_SHIFT, ORTH_SHIFT_MIXED
 
 
 # ---------------------------------------------------------------- small helpers

@@ -276,20 +276,20 @@ svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout
 // the columns of L^{-1} (one thread per column).  Used so that Y W has
 // orthonormal columns when G = Y^H Y; the shift keeps it well defined for
 // rank-deficient Y and damps directions below shift * max G_ii smoothly.
-template <typename C>
+template <typename C, typename GIN>
 __global__ void __launch_bounds__(JAC_THREADS)
-chol_w_kernel(const cd* Gin, int n, double shift, C* Wout, cd* work, int use_smem) {
+chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, cd* work, int use_smem) {
   extern __shared__ double4 smraw4[];
   __shared__ double red[JAC_THREADS / 32];
   __shared__ double sh_s;
   const int b = blockIdx.x, tid = threadIdx.x;
   cd* L = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * 2 * n * n;
   cd* X = L + (long long)n * n;
-  const cd* G = Gin + (long long)b * n * n;
+  const GIN* G = Gin + (long long)b * n * n;
   double mx = 0.0;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     int i = idx / n, j = idx % n;
-    cd g = G[idx];
+    cd g = to_cd(G[idx]);
     L[idx] = (j <= i) ? g : mk(0.0, 0.0);
     if (i == j) mx = fmax(mx, g.x);
   }
@@ -343,7 +343,7 @@ chol_w_kernel(const cd* Gin, int n, double shift, C* Wout, cd* work, int use_sme
   }
 }
 
-cudaError_t chol_w_batched(const cd* G, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, cd* work,
                            cudaStream_t st) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   size_t bytes = (size_t)2 * n * n * sizeof(cd);
@@ -351,14 +351,20 @@ cudaError_t chol_w_batched(const cd* G, int n, int batch, double shift, void* W,
   if (!use_smem && !work) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(chol_w_kernel<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    cudaFuncSetAttribute(chol_w_kernel<cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cd, cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cf, cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cf, cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
     attr = true;
   }
-  if (w_f64)
-    chol_w_kernel<cd><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(G, n, shift, (cd*)W, work, use_smem);
+  const size_t sm = use_smem ? bytes : 0;
+  if (w_f64 && g_f64)
+    chol_w_kernel<cd, cd><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, work, use_smem);
+  else if (g_f64)
+    chol_w_kernel<cf, cd><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cf*)W, work, use_smem);
+  else if (!w_f64)
+    chol_w_kernel<cf, cf><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, work, use_smem);
   else
-    chol_w_kernel<cf><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(G, n, shift, (cf*)W, work, use_smem);
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

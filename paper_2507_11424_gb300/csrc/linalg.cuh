@@ -20,7 +20,8 @@ cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double*
 // L L^H = G + shift * max_i G_ii * I, batched n x n (contiguous); W written as
 // complex128 (w_f64) or complex64.  work: >= batch * 2 n^2 complex when
 // !chol_fits_smem(n).
-cudaError_t chol_w_batched(const cd* G, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+// G is complex128 (g_f64) or complex64; the factorisation always runs in FP64.
+cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, cd* work,
                            cudaStream_t st);
 bool chol_fits_smem(int n);
 

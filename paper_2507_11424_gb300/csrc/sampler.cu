@@ -23,7 +23,8 @@
 namespace tns {
 
 static constexpr double ORTH_SHIFT_FP64 = 1e-14;
-static constexpr double ORTH_SHIFT_MIXED = 1e-8;
+static constexpr double ORTH_SHIFT_CQR_FIRST = 1e-5;
+static constexpr double ORTH_SHIFT_CQR_NEXT = 1e-7;
 
 static inline int nblk(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 1 << 20); }
 
@@ -51,6 +52,11 @@ __global__ void omega_kernel(C* out, int n, int kk, uint64_t seed, int stage, in
     double re = 2.0 * u53(w.v[0], w.v[1]) - 1.0, im = 2.0 * u53(w.v[2], w.v[3]) - 1.0;
     out[idx] = from_cd<C>(mk(re, im));
   }
+}
+
+__global__ void widen_kernel(const cf* in, cd* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_double2(in[i].x, in[i].y);
 }
 
 // UBt[b][i][r] = UB[b][i][r] for r < Rk (first Rk eigenvectors, descending).
@@ -255,14 +261,11 @@ struct Ctx {
   tns_state* s;
   cudaStream_t st;
   bool f64;
-  Prec gp, gram;
+  Prec gp;
   size_t esz;
   uint64_t seed;
   int R;
-  // Shift of the Cholesky orthonormalisation, relative to max_i G_ii: 1e-14 in FP64
-  // (100x the rounding floor of an FP64 Gram); 1e-8 in the mixed path, where the
-  // FP32 product Y W amplifies rounding by (shift)^{-1/2} ~ 1e4.
-  double orth_shift;
+
 };
 
 static long long label_stride(const TView& v, char l) {
@@ -404,22 +407,36 @@ static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
   return TNS_OK;
 }
 
-// Orthonormalising map W (kk x kk): Y W has orthonormal columns, from the Gram
-// matrix G = Y^H Y (FP64) by a shifted Cholesky factorisation
-// L L^H = G + orth_shift * max_i G_ii * I, W = L^{-H}.
-static tns_status orth_w(Ctx& cx, void* Y, long long S, long long M, int kk, void* Wout) {
+// Q = orthonormal basis of range(Y) for each batch entry (Y, Q: S x M x kk).
+// FP64 path: W = L^{-H} with L L^H = Y^H Y + 1e-14 max_i G_ii (the shift only
+// regularises rank-deficient Y), Q = Y W.  Mixed path: shifted CholeskyQR3 in
+// FP32 (Gram and products in FP32, the kk x kk Cholesky in FP64): a first pass
+// with shift 1e-5 gives a well-conditioned basis of the same range, two more
+// passes restore orthonormality to FP32 accuracy without damping any direction.
+static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void* Qout) {
   tns_state* s = cx.s;
-  cd* G;
-  TNS_TRY(wsget(s, "z_G", sizeof(cd) * S * kk * kk, (void**)&G));
-  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Y, "Smc", {S, M, kk}, true), view(Y, "Sme", {S, M, kk}),
-                         view(G, "Sce", {S, kk, kk}), cx.gram));
+  void *G, *Wm;
+  TNS_TRY(wsget(s, "z_G", sizeof(cd) * S * kk * kk, &G));
+  TNS_TRY(wsget(s, "z_W", cx.esz * S * kk * kk, &Wm));
   cd* work = nullptr;
   if (!chol_fits_smem(kk)) TNS_TRY(wsget(s, "z_cwork", sizeof(cd) * S * 2 * kk * kk, (void**)&work));
-  cudaEvent_t ev = s->prof.begin(cx.st);
-  TNS_TRY_CUDA(chol_w_batched(G, kk, (int)S, cx.orth_shift, Wout, cx.f64, work, cx.st));
-  s->prof.end(PC_EIGH, ev, 0.0, cx.st);
-  s->launches++;
-  return TNS_OK;
+  auto pass = [&](void* src, void* dst, double shift) -> tns_status {
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(src, "Smc", {S, M, kk}, true), view(src, "Sme", {S, M, kk}),
+                           view(G, "Sce", {S, kk, kk}), cx.gp));
+    cudaEvent_t ev = s->prof.begin(cx.st);
+    TNS_TRY_CUDA(chol_w_batched(G, cx.f64, kk, (int)S, shift, Wm, cx.f64, work, cx.st));
+    s->prof.end(PC_EIGH, ev, 0.0, cx.st);
+    s->launches++;
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(src, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
+                           view(dst, "Sme", {S, M, kk}), cx.gp));
+    return TNS_OK;
+  };
+  if (cx.f64) return pass(Y, Qout, ORTH_SHIFT_FP64);
+  void* tmp;
+  TNS_TRY(wsget(s, "z_Q2", cx.esz * S * M * kk, &tmp));
+  TNS_TRY(pass(Y, Qout, ORTH_SHIFT_CQR_FIRST));
+  TNS_TRY(pass(Qout, tmp, ORTH_SHIFT_CQR_NEXT));
+  return pass(tmp, Qout, ORTH_SHIFT_CQR_NEXT);
 }
 
 // Rank-R factorisation T = K C of each batch entry (T: S x M x N): randomized
@@ -435,12 +452,11 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   const int kk = (int)std::min<long long>(std::min<long long>(cx.R + 8, M), N);
   const int Rk = (int)std::min<long long>(std::min<long long>(cx.R, M), N);
   *Rk_out = Rk;
-  void *Y, *Q, *Z, *B, *Wm, *UBt, *om;
+  void *Y, *Q, *Z, *B, *UBt, *om;
   TNS_TRY(wsget(s, "z_Y", cx.esz * S * M * kk, &Y));
   TNS_TRY(wsget(s, "z_Q", cx.esz * S * M * kk, &Q));
   TNS_TRY(wsget(s, "z_Z", cx.esz * S * N * kk, &Z));
   TNS_TRY(wsget(s, "z_B", cx.esz * S * N * kk, &B));
-  TNS_TRY(wsget(s, "z_W", cx.esz * S * kk * kk, &Wm));
   TNS_TRY(wsget(s, "z_UBt", cx.esz * S * kk * kk, &UBt));
   void* Ymat = Y;
   if (kk == N) {
@@ -454,20 +470,14 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     s->launches++;
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}),
                            cx.gp));
-    TNS_TRY(orth_w(cx, Y, S, M, kk, Wm));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Y, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
-                           view(Q, "Sme", {S, M, kk}), cx.gp));
+    TNS_TRY(orth(cx, Y, S, M, kk, Q));
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}, true), view(Q, "Sme", {S, M, kk}),
                            view(Z, "Sne", {S, N, kk}), cx.gp));
-    TNS_TRY(orth_w(cx, Z, S, N, kk, Wm));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Z, "Snc", {S, N, kk}), view(Wm, "Sce", {S, kk, kk}),
-                           view(B, "Sne", {S, N, kk}), cx.gp));
+    TNS_TRY(orth(cx, Z, S, N, kk, B));
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(B, "Sne", {S, N, kk}),
                            view(Y, "Sme", {S, M, kk}), cx.gp));
   }
-  TNS_TRY(orth_w(cx, Ymat, S, M, kk, Wm));
-  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Ymat, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
-                         view(Q, "Sme", {S, M, kk}), cx.gp));
+  TNS_TRY(orth(cx, Ymat, S, M, kk, Q));
   TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Q, "Sme", {S, M, kk}, true), view(T, "Smn", {S, M, N}),
                          view(B, "Sen", {S, kk, N}), cx.gp));
   cd *Hm, *V;
@@ -477,8 +487,18 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   TNS_TRY(wsget(s, "z_V2", sizeof(cd) * S * kk * kk, (void**)&V));
   TNS_TRY(wsget(s, "z_mu", sizeof(double) * S * kk, (void**)&mu));
   TNS_TRY(wsget(s, "z_status2", sizeof(int) * S, (void**)&status));
-  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
-                         view(Hm, "Sef", {S, kk, kk}), cx.gram));
+  // B B^H: FP64 in the FP64 path; FP32 in the mixed path, widened for the FP64 eigensolver
+  if (cx.f64) {
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
+                           view(Hm, "Sef", {S, kk, kk}), cx.gp));
+  } else {
+    void* H32;
+    TNS_TRY(wsget(s, "z_H32", sizeof(cf) * S * kk * kk, &H32));
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
+                           view(H32, "Sef", {S, kk, kk}), cx.gp));
+    widen_kernel<<<nblk(S * kk * kk), 256, 0, cx.st>>>((const cf*)H32, Hm, S * kk * kk);
+    s->launches++;
+  }
   cd* work = nullptr;
   if (!jacobi_fits_smem(kk, kk)) {
     long long np = kk + (kk & 1);
@@ -704,11 +724,9 @@ static tns_status make_ctx(tns_state* s, int chi_b, uint64_t seed, Ctx& cx) {
   cx.st = s->st;
   cx.f64 = (s->prec == TNS_PREC_FP64);
   cx.gp = cx.f64 ? Prec::F64 : Prec::F32;
-  cx.gram = cx.f64 ? Prec::F64 : Prec::F32_ACC64;
   cx.esz = cx.f64 ? sizeof(cd) : sizeof(cf);
   cx.seed = seed;
   cx.R = chi_b;
-  cx.orth_shift = cx.f64 ? ORTH_SHIFT_FP64 : ORTH_SHIFT_MIXED;
   return ensure_work_cells(s, cx.f64);
 }
 

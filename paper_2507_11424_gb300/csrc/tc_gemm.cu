@@ -129,8 +129,11 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long m0 = (long long)blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
+  // linear grid, N tiles fastest: the CTAs sharing an A row-block run together and
+  // read it from L2 instead of re-reading it from HBM once per N tile
+  const int ntn = (Nr + BN - 1) / BN;
+  const long long m0 = (long long)(blockIdx.x / ntn) * BM;
+  const int n0 = (int)(blockIdx.x % ntn) * BN;
   const int nkb = (Kr + BKF - 1) / BKF;
   const int nsteps = 3 * nkb;
 
@@ -313,8 +316,9 @@ cudaError_t tc_gemm_tf32x3(const float* A, const float* Alo, long long M, int Kr
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Nr + BN - 1) / BN));
-  tc_gemm_tf32x3_kernel<<<grid, 128, SMEM_BYTES, st>>>(ma, malo, mbhi, mblo, C, ldc, M, Nr, Kr, err);
+  const long long tiles = ((M + BM - 1) / BM) * ((Nr + BN - 1) / BN);
+  if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
+  tc_gemm_tf32x3_kernel<<<(unsigned)tiles, 128, SMEM_BYTES, st>>>(ma, malo, mbhi, mblo, C, ldc, M, Nr, Kr, err);
   return cudaGetLastError();
 }
 

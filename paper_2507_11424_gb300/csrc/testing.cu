@@ -71,7 +71,7 @@ extern "C" tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, con
   cudaStream_t st = (cudaStream_t)stream;
   cd* work = nullptr;
   if (!chol_fits_smem(n)) TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * 2 * (long long)n * n));
-  cudaError_t e = chol_w_batched((const cd*)G, n, batch, shift, W, true, work, st);
+  cudaError_t e = chol_w_batched(G, true, n, batch, shift, W, true, work, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(work);
   TNS_TRY_CUDA(e);

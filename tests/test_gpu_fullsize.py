@@ -36,7 +36,7 @@ def state(tmp_path_factory):
 # different range-finder test matrix already moves single conditionals by ~2.6e-2;
 # FP32 rounding moves them by ~2e-3 at most.  The mixed bar is 5e-3 on the largest
 # conditional and 5e-4 on the mean over all conditionals of the sample.
-@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT_MIXED, 5e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
+@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT, 5e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
 def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
     st, t, cfg, bits = state
     R = cfg["chi_b"]

@@ -145,7 +145,7 @@ def test_sampler_matches_oracle_config1(pkg, tmp_path, prec, tol, tc):
     seed, n = 20250711, 48
     xs, logq, cond = st.sample(chi_b=16, n=n, seed=seed, cond=True)
     xs, logq, cond = xs.cpu().numpy(), logq.cpu().numpy(), cond.cpu().numpy()
-    cut = bmps.ORTH_SHIFT if prec == "fp64" else bmps.ORTH_SHIFT_MIXED
+    cut = bmps.ORTH_SHIFT
     _, lq_o, q0_o = bmps.sample(t, 16, 0, seed, forced=xs, gram_cut=cut)
     assert np.abs(cond - q0_o).max() < tol
     assert np.abs(logq - lq_o).max() < 20 * tol
@@ -256,5 +256,5 @@ def test_tensor_core_path_matches_cuda_cores(pkg, tmp_path):
     st.set_tensor_cores(False)
     xs2, lq2, c2 = st.sample(R, n, seed, cond=True)
     assert np.abs(c1.cpu().numpy() - c2.cpu().numpy()).max() < 1e-4
-    _, lq_o, q0_o = bmps.sample(t, R, 0, seed, forced=xs.cpu().numpy(), gram_cut=bmps.ORTH_SHIFT_MIXED)
+    _, lq_o, q0_o = bmps.sample(t, R, 0, seed, forced=xs.cpu().numpy(), gram_cut=bmps.ORTH_SHIFT)
     assert np.abs(c1.cpu().numpy() - q0_o).max() < 1e-4
