@@ -10,6 +10,8 @@ from .circuits import (  # noqa: F401
     heisenberg_circuit, lucj_like_circuit, random_su4_circuit, flatten_group,
 )
 
+from .made_init import made_init, epoch_orders  # noqa: F401
+
 # Named configurations (sizes of the paper-shaped synthetic workloads).
 CONFIGS = {
     "sq4x4": dict(lattice=("square", 4, 4), layers=4, dt=0.2, chi=4, chi_b=16, n_samples=1024),
