@@ -213,6 +213,89 @@ tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_m
 tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
                             void* cuda_stream);
 
+/*
+ * Learned proposal and independent Metropolis-Hastings.  The paper samples only
+ * with the boundary-MPS sampler above; these calls add an optional second stage:
+ * a MADE network (masked autoregressive MLP: Germain, Gregor, Murray and
+ * Larochelle, ICML 2015) fitted by maximum likelihood to the sampler's
+ * bitstrings, whose cheap exact samples and log-probabilities log g(x) feed an
+ * independent Metropolis-Hastings chain with target p(x) = |<x|psi>|^2 (log p
+ * from tns_amplitude).
+ *
+ * Network: n inputs in natural qubit order, three ReLU hidden layers of width h,
+ * n logits; g(x_i = 1 | x_<i) = sigmoid(l_i).  Degrees: input/output i -> i+1,
+ * hidden unit k -> 1 + (k mod (n-1)).  Hidden masks keep weight (k, j) iff
+ * deg(k) >= deg(j); the output mask keeps (i, k) iff i+1 > deg(k).  Parameters
+ * are packed float32: W1[h][n], b1[h], W2[h][h], b2[h], W3[h][h], b3[h],
+ * W4[n][h], b4[n] (P = 2hn + 2h^2 + 3h + n floats).
+ * Arithmetic: FP32 master weights and Adam moments; GEMM operands (masked
+ * weights, activations, back-propagated errors) rounded to BF16, products
+ * accumulated in FP32; log g and the MH acceptance test in FP64.
+ * Bit buffers are device uint8 [rows][n], one byte per qubit (0 or 1).
+ * A tns_made is used by one host thread at a time and runs on the stream given
+ * at creation; every call returns after that stream has finished the call's work.
+ */
+typedef struct tns_made tns_made; /* opaque, library-owned */
+
+/*
+ * tns_made_create -- allocate a network with the given initial parameters.
+ *   n_sites >= 2, hidden >= 1; params_host  host float32 [P], copied.
+ *   cuda_stream  stream for every later call on this network.
+ */
+tns_status tns_made_create(int32_t n_sites, int32_t hidden, const float* params_host, void* cuda_stream,
+                           tns_made** out);
+
+/* tns_made_params -- copy the current FP32 parameters to params_host [P]. */
+tns_status tns_made_params(const tns_made* m, float* params_host);
+
+/*
+ * tns_made_train -- mini-batch Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * mean negative log-likelihood.  Epoch e visits the rows of bits_dev [n][n_sites]
+ * in the order orders_host[e*n .. e*n+n-1] (host int32, NULL = natural order),
+ * in consecutive batches of `batch` rows (the last may be shorter).  The Adam
+ * step count carries over between calls.  loss_host (host float64 [epochs] or
+ * NULL) receives, per epoch, the mean NLL of each row under the parameters
+ * before the step of its batch.
+ */
+tns_status tns_made_train(tns_made* m, const uint8_t* bits_dev, int64_t n, int32_t batch, int32_t epochs,
+                          const int32_t* orders_host, float lr, double* loss_host);
+
+/*
+ * tns_made_grad -- gradient of the mean NLL over the n rows of bits_dev
+ * (1 <= n <= 2^20) into grad_host (host float32 [P], or NULL); the mean NLL into
+ * *loss (or NULL).  Masked-out weights get gradient 0.  Parameters unchanged.
+ */
+tns_status tns_made_grad(tns_made* m, const uint8_t* bits_dev, int64_t n, float* grad_host, double* loss);
+
+/* tns_made_logprob -- log g(x) (device float64 [n]) of the n rows of bits_dev. */
+tns_status tns_made_logprob(tns_made* m, const uint8_t* bits_dev, int64_t n, double* logg_dev);
+
+/*
+ * tns_made_sample -- n ancestral samples into bits_dev [n][n_sites] and their
+ * log g into logg_dev [n].  Qubit i of sample s is 1 iff u >= g(x_i = 0 | x_<i),
+ * u = the 53-bit uniform of Philox4x32-10 words (0, 1) at counter
+ * (s mod 2^32, s div 2^32, i, 1) under key (seed mod 2^32, seed div 2^32).
+ */
+tns_status tns_made_sample(tns_made* m, int64_t n, uint64_t seed, uint8_t* bits_dev, double* logg_dev);
+
+void tns_made_destroy(tns_made* m);
+
+/*
+ * tns_mh_independent -- n_chains independent Metropolis-Hastings chains over
+ * precomputed proposals.  Chain c at step t proposes proposal (c, t) with target
+ * log-probability logp_prop_dev[c*n_steps+t] and proposal log-probability
+ * logg_prop_dev[...] (device float64 [n_chains][n_steps]); the chain starts
+ * from a state with log p = logp0_dev[c], log g = logg0_dev[c].  The proposal is
+ * accepted iff log u < (lp' - lp) + (lg - lg'), u as in tns_made_sample at
+ * counter (c, t, 0, 2) (u = 0 always accepts).  Outputs: state_dev (device int32
+ * [n_chains][n_steps]) = index t' of the proposal chain c holds after step t,
+ * -1 while it holds its initial state; accepted_dev (device int64 [n_chains]) =
+ * accepted moves.  Log-probabilities may be unnormalised (constants cancel).
+ */
+tns_status tns_mh_independent(int32_t n_chains, int32_t n_steps, const double* logp_prop_dev,
+                              const double* logg_prop_dev, const double* logp0_dev, const double* logg0_dev,
+                              uint64_t seed, int32_t* state_dev, int64_t* accepted_dev, void* cuda_stream);
+
 void tns_destroy(tns_state* s);
 const char* tns_last_error(void);
 

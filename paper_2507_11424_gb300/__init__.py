@@ -18,7 +18,7 @@ import numpy as np
 from . import _native
 from ._native import PREC, TNSError, check, load  # noqa: F401
 
-__all__ = ["TNSState", "TNSError", "load", "pack_group"]
+__all__ = ["TNSState", "MADE", "mh_independent", "TNSError", "load", "pack_group"]
 
 
 def _torch():
@@ -183,3 +183,85 @@ class TNSState:
         check(self.lib.tns_amplitude(self._h, int(chi_b), int(n), C.c_void_p(bits.data_ptr()),
                                      C.c_void_p(la.data_ptr()), C.c_void_p(ph.data_ptr())), "tns_amplitude")
         return la, ph
+
+
+class MADE:
+    """Learned autoregressive proposal (tns_made_* in include/tns.h), on the current GPU."""
+
+    def __init__(self, n_sites: int, hidden: int, params, stream=None):
+        self.lib = load()
+        self.n, self.h = int(n_sites), int(hidden)
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        if p.size != self.n_params(self.n, self.h):
+            raise ValueError(f"expected {self.n_params(self.n, self.h)} parameters, got {p.size}")
+        self._h = C.c_void_p()
+        check(self.lib.tns_made_create(self.n, self.h, _ptr(p), _stream_handle(stream), C.byref(self._h)),
+              "tns_made_create")
+
+    @staticmethod
+    def n_params(n: int, h: int) -> int:
+        return 2 * h * n + 2 * h * h + 3 * h + n
+
+    def close(self):
+        if self._h:
+            self.lib.tns_made_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params(self.n, self.h), dtype=np.float32)
+        check(self.lib.tns_made_params(self._h, _ptr(out)), "tns_made_params")
+        return out
+
+    def train(self, bits, batch: int, epochs: int, lr: float = 1e-3, orders=None) -> np.ndarray:
+        """Adam on the mean NLL of the rows of bits (torch uint8 CUDA [n, n_sites]); per-epoch losses."""
+        n = int(bits.shape[0])
+        losses = np.zeros(max(epochs, 1), dtype=np.float64)
+        od = None
+        if orders is not None:
+            od = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(epochs, n))
+        check(self.lib.tns_made_train(self._h, C.c_void_p(bits.data_ptr()), n, int(batch), int(epochs),
+                                      _ptr(od) if od is not None else None, float(lr), _ptr(losses)),
+              "tns_made_train")
+        return losses[:epochs]
+
+    def grad(self, bits):
+        g = np.zeros(self.n_params(self.n, self.h), dtype=np.float32)
+        loss = C.c_double()
+        check(self.lib.tns_made_grad(self._h, C.c_void_p(bits.data_ptr()), int(bits.shape[0]), _ptr(g),
+                                     C.byref(loss)), "tns_made_grad")
+        return loss.value, g
+
+    def log_prob(self, bits):
+        torch = _torch()
+        out = torch.zeros(int(bits.shape[0]), dtype=torch.float64, device="cuda")
+        check(self.lib.tns_made_logprob(self._h, C.c_void_p(bits.data_ptr()), int(bits.shape[0]),
+                                        C.c_void_p(out.data_ptr())), "tns_made_logprob")
+        return out
+
+    def sample(self, n: int, seed: int):
+        torch = _torch()
+        bits = torch.zeros((n, self.n), dtype=torch.uint8, device="cuda")
+        logg = torch.zeros(n, dtype=torch.float64, device="cuda")
+        check(self.lib.tns_made_sample(self._h, int(n), C.c_uint64(int(seed) & (2**64 - 1)),
+                                       C.c_void_p(bits.data_ptr()), C.c_void_p(logg.data_ptr())), "tns_made_sample")
+        return bits, logg
+
+
+def mh_independent(logp_prop, logg_prop, logp0, logg0, seed: int, stream=None):
+    """Independent MH chains over precomputed proposals (torch float64 CUDA tensors
+    [C, T], [C, T], [C], [C]); returns (state int32 [C, T], accepted int64 [C])."""
+    torch = _torch()
+    Cn, T = logp_prop.shape
+    tensors = [t.contiguous() for t in (logp_prop, logg_prop, logp0, logg0)]
+    state = torch.empty((Cn, T), dtype=torch.int32, device="cuda")
+    acc = torch.empty(Cn, dtype=torch.int64, device="cuda")
+    check(load().tns_mh_independent(int(Cn), int(T), *[C.c_void_p(t.data_ptr()) for t in tensors],
+                                    C.c_uint64(int(seed) & (2**64 - 1)), C.c_void_p(state.data_ptr()),
+                                    C.c_void_p(acc.data_ptr()), _stream_handle(stream)), "tns_mh_independent")
+    return state, acc
