@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=150.0)
+    ap.add_argument("--state-cache", default=None,
+                    help="TNSF file: load the state from it when present, else build it and save it there")
     return ap.parse_args()
 
 
@@ -193,10 +195,17 @@ def run_gpu(args):
     cfg, lat, bits, groups = workload()
     chi, R, B = cfg["chi"], cfg["chi_b"], args.batch
     t0 = time.time()
-    st = pkg.TNSState(lat.grid_rc, lat.edges, bits, chi_max=chi, prec=args.prec)
-    for g in groups:
-        st.apply_gate_layer(g, chi=chi)
-        st.bp_gauge(300, 1e-10)
+    if args.state_cache and os.path.exists(args.state_cache):
+        st = pkg.TNSState.load_file(args.state_cache)
+        st.n = lat.n_qubits
+        st.set_precision(args.prec)
+    else:
+        st = pkg.TNSState(lat.grid_rc, lat.edges, bits, chi_max=chi, prec=args.prec)
+        for g in groups:
+            st.apply_gate_layer(g, chi=chi)
+            st.bp_gauge(300, 1e-10)
+        if args.state_cache:
+            st.save(args.state_cache)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     t0 = time.time()
@@ -287,7 +296,9 @@ def run_gpu(args):
         "clocks": clk,
         "gpu_launches": launches,
         "boundary_mps_tflops": total_flops / (ms / 1e3) / 1e12,
-        "profile_ms": {k: round(v["ms"], 2) for k, v in prof.items()},
+        "profile": {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
+                        "tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 2) if v["ms"] > 0 and v["flops"] else None}
+                    for k, v in prof.items() if v["launches"]},
         "state_build_s": round(build_s, 2), "env_build_s": round(env_s, 3), "log_norm": log_norm,
         "log_fidelity": st.log_fidelity(), "sector_fraction": sector,
     }

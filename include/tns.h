@@ -178,9 +178,12 @@ tns_status tns_launch_count(const tns_state* s, int64_t* launches);
  * Classes: 0 = environment contractions (the row's norm-environment GEMMs of
  * the marginal sweeps), 1 = other marginal-sweep contractions, 2 = zip-up
  * compression contractions, 3 = FP64 factorisations (Cholesky, Jacobi), 4 =
- * fused marginal/draw/project kernel, 5 = tensor-core operand preparation
- * (TF32 remainders and the real block expansion of the environments).  tns_profile_enable(s, 1) also clears the
- * counters.
+ * fused marginal/draw/project kernel, 5/6/7 = tensor-core operand packing
+ * (gathers and the real block expansion with TF32 remainders) for classes
+ * 0/1/2, 8/9 = zip / other sweep contractions of the mixed path that ran on
+ * the CUDA cores (too small for the tensor-core kernel).  With tensor cores
+ * on, classes 0-2 time the GEMM kernel alone.  tns_profile_enable(s, 1) also
+ * clears the counters.
  */
 tns_status tns_profile_enable(tns_state* s, int32_t enable);
 tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_ms, int64_t* launches,

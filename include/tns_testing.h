@@ -26,6 +26,13 @@ tns_status tns_test_philox(int64_t n, const uint32_t* ctr_key_dev, uint32_t* out
 tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
                          void* cuda_stream);
 
+/* The FP32 variant of the eigensolver used by the mixed-precision truncation:
+ * A_dev complex64 [batch][n][n] Hermitian (read only), lam_dev float64 [batch][n]
+ * descending, V_dev complex128 [batch][n][n] (column j = eigenvector j).  Sweep
+ * counts are reported through tns_test_eigh_sweeps like tns_test_eigh's. */
+tns_status tns_test_eigh32(int32_t batch, int32_t n, const float* A_dev, double* lam_dev, double* V_dev,
+                           void* cuda_stream);
+
 /* Sweeps used by each matrix of the last tns_test_eigh call (host int32 [batch]);
  * a value of 0 or less means the sweep cap was reached. */
 tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* sweeps_host);
@@ -36,13 +43,26 @@ tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* sweeps_host);
 tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, const double* G_dev, double* W_dev,
                           void* cuda_stream);
 
-/* Tensor-core complex GEMM used by the mixed-precision marginal sweeps:
+/* Tensor-core complex GEMM used by the mixed-precision contractions:
  * C = A B^T with A complex64 [M][K], B complex64 [N][K] (K contiguous), C complex64
  * [M][N], computed by tcgen05 kind::tf32 with a three-pass hi/lo split.
  * Returns TNS_ERR_STATE when the shape is not supported by the tensor-core path
- * (K odd or below 16) and TNS_ERR_NUMERIC when a pipeline wait timed out. */
+ * and TNS_ERR_NUMERIC when a pipeline wait timed out. */
 tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const float* A_dev, const float* B_dev, float* C_dev,
                            void* cuda_stream);
+
+/* The library's labelled tensor contraction C[c] = sum A[a] B[b] (einsum over the
+ * label strings: labels in all three operands are batch indices, labels in one
+ * input and C are free, labels in both inputs only are summed).  Each operand is
+ * given by its labels (one char per axis), extents and strides (in complex
+ * elements) and a conjugation flag; C is overwritten.
+ *   mode 0: complex64 on the CUDA cores; 1: complex64 on the tensor cores
+ *           (TNS_ERR_STATE if the contraction does not fit that path);
+ *           2: complex128 on the CUDA cores. */
+tns_status tns_test_contract(const char* labels_a, const int64_t* dims_a, const int64_t* strides_a, int32_t conj_a,
+                             const void* A_dev, const char* labels_b, const int64_t* dims_b, const int64_t* strides_b,
+                             int32_t conj_b, const void* B_dev, const char* labels_c, const int64_t* dims_c,
+                             const int64_t* strides_c, void* C_dev, int32_t mode, void* cuda_stream);
 
 /* Batched FP64 thin SVD A = U diag(s) V^H (m >= n) by one-sided Jacobi.
  *   A_dev  device complex128 [batch][m][n] (read only); s_dev float64 [batch][n];

@@ -133,7 +133,8 @@ class TNSState:
         check(self.lib.tns_launch_count(self._h, C.byref(v)), "tns_launch_count")
         return v.value
 
-    PROFILE_CLASSES = ("env_gemm", "sweep_gemm", "zip_gemm", "eigh", "marginal", "tc_prep")
+    PROFILE_CLASSES = ("env_gemm", "sweep_gemm", "zip_gemm", "eigh", "marginal", "tc_prep", "tc_prep_sweep",
+                       "tc_prep_zip", "zip_simt", "sweep_simt")
 
     def set_tensor_cores(self, enable: bool):
         check(self.lib.tns_set_tensor_cores(self._h, 1 if enable else 0), "tns_set_tensor_cores")

@@ -59,6 +59,14 @@ void Profiler::end(int cls, cudaEvent_t a, double fl, cudaStream_t st) {
   pending.push_back({cls, a, e, fl});
 }
 
+void Profiler::span(int cls, cudaEvent_t a, cudaEvent_t b, double fl, bool own_a, bool own_b) {
+  if (!on || !a || !b) return;
+  Rec r{cls, a, b, fl};
+  r.own_a = own_a;
+  r.own_b = own_b;
+  pending.push_back(r);
+}
+
 void Profiler::resolve() {
   for (auto& r : pending) {
     float t = 0.f;
@@ -67,8 +75,11 @@ void Profiler::resolve() {
       flops[r.cls] += r.flops;
       n[r.cls] += 1;
     }
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+  }
+  // destroy after every interval is read (an event may end one span and start the next)
+  for (auto& r : pending) {
+    if (r.own_a) cudaEventDestroy(r.a);
+    if (r.own_b) cudaEventDestroy(r.b);
   }
   pending.clear();
 }

@@ -1,5 +1,6 @@
 // Strided tensor-contraction GEMM (SIMT) and the host planner.  See contract.cuh.
 #include "contract.cuh"
+#include "tc_gemm.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -278,6 +279,237 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(const GemmParams p, 
   }
 }
 
+// ------------------------------------------------------ tensor-core operand packing
+// Operand offsets of batch entry b (A side when which == 0, B side otherwise).
+__device__ inline long long batch_off(const GemmParams& p, long long b, int which) {
+  long long o = 0;
+  int bi[2] = {0, 0};
+  for (int g = 0; g < p.nb; ++g) {
+    bi[g] = (int)(b % p.bdim[g]);
+    b /= p.bdim[g];
+    o += bi[g] * (which == 0 ? p.sAb[g] : p.sBb[g]);
+  }
+  if (which == 0) {
+    if (p.aidx) o += (long long)p.aidx[(long long)bi[p.a_idx_grp] * p.a_idx_ld] * p.a_idx_stride;
+    if (p.aoff) o += p.aoff[bi[p.aoff_grp]];
+  } else {
+    if (p.bidx) o += (long long)p.bidx[(long long)bi[p.b_idx_grp] * p.b_idx_ld] * p.b_idx_stride;
+    if (p.boffs) o += p.boffs[bi[p.boff_grp]];
+  }
+  return o;
+}
+__device__ inline long long decomp(long long i, int n, const int* dim, const long long* stride) {
+  long long o = 0;
+  for (int g = 0; g < n; ++g) {
+    o += (i % dim[g]) * stride[g];
+    i /= dim[g];
+  }
+  return o;
+}
+// TF32 split of an FP32 value: hi = tf32_rn(v), lo = tf32_rn(v - hi).
+__device__ inline float tf32_lo_rn(float v) { return tf32_rn(v - tf32_rn(v)); }
+
+// A side: [nbA][M][Kp] interleaved complex, zero beyond 2K.
+__global__ void pack_a_kernel(const GemmParams p, long long nbA, int Kp, float* __restrict__ out) {
+  const int Kc = Kp / 2;
+  const long long tot = nbA * p.M * Kc;
+  const float2* A = (const float2*)p.A;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int kc = (int)(i % Kc);
+    const long long r = i / Kc;
+    float2 v = make_float2(0.f, 0.f);
+    if (kc < p.K) {
+      const long long b = r / p.M, m = r % p.M;
+      v = A[batch_off(p, b, 0) + decomp(m, p.nm, p.mdim, p.sAm) + decomp(kc, p.nk, p.kdim, p.sAk)];
+      if (p.conjA) v.y = -v.y;
+    }
+    *reinterpret_cast<float2*>(out + r * Kp + 2 * kc) = v;
+  }
+}
+
+// B side: the real block expansion, hi/lo [nbB][2N][Kp] (TF32 split, see
+// tc_gemm.cu); rows 2n / 2n+1 hold (Br, -Bi) / (Bi, Br) of column n interleaved by k.
+__global__ void pack_b_kernel(const GemmParams p, long long nbB, int Kp, float* __restrict__ hi, float* __restrict__ lo) {
+  const int Kc = Kp / 2;
+  const long long tot = nbB * (long long)p.N * Kc;
+  const float2* B = (const float2*)p.B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int kc = (int)(i % Kc);
+    const long long r = i / Kc;            // b * N + n
+    float2 v = make_float2(0.f, 0.f);
+    if (kc < p.K) {
+      const long long b = r / p.N, n = r % p.N;
+      v = B[batch_off(p, b, 1) + decomp(n, p.nn, p.ndim, p.sBn) + decomp(kc, p.nk, p.kdim, p.sBk)];
+      if (p.conjB) v.y = -v.y;
+    }
+    const long long o0 = (2 * r) * Kp + 2 * kc, o1 = o0 + Kp;
+    const float hx = tf32_rn(v.x), hy = tf32_rn(v.y), lx = tf32_lo_rn(v.x), ly = tf32_lo_rn(v.y);
+    *reinterpret_cast<float2*>(hi + o0) = make_float2(hx, -hy);
+    *reinterpret_cast<float2*>(hi + o1) = make_float2(hy, hx);
+    *reinterpret_cast<float2*>(lo + o0) = make_float2(lx, -ly);
+    *reinterpret_cast<float2*>(lo + o1) = make_float2(ly, lx);
+  }
+}
+
+static unsigned grid_for(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32));
+}
+
+// Swap the roles of A and B (C^T = B^T A^T): M <-> N.
+static void swap_roles(GemmParams& p) {
+  GemmParams q = p;
+  q.M = p.N;
+  q.N = (int)p.M;
+  q.nm = p.nn; q.nn = p.nm;
+  for (int g = 0; g < 4; ++g) {
+    q.mdim[g] = p.ndim[g]; q.ndim[g] = p.mdim[g];
+    q.sAm[g] = p.sBn[g]; q.sCm[g] = p.sCn[g];
+    q.sBn[g] = p.sAm[g]; q.sCn[g] = p.sCm[g];
+    q.sAk[g] = p.sBk[g]; q.sBk[g] = p.sAk[g];
+  }
+  for (int g = 0; g < 2; ++g) { q.sAb[g] = p.sBb[g]; q.sBb[g] = p.sAb[g]; }
+  q.aidx = p.bidx; q.a_idx_ld = p.b_idx_ld; q.a_idx_stride = p.b_idx_stride; q.a_idx_grp = p.b_idx_grp;
+  q.bidx = p.aidx; q.b_idx_ld = p.a_idx_ld; q.b_idx_stride = p.a_idx_stride; q.b_idx_grp = p.a_idx_grp;
+  q.aoff = p.boffs; q.aoff_grp = p.boff_grp;
+  q.boffs = p.aoff; q.boff_grp = p.aoff_grp;
+  q.A = p.B; q.B = p.A;
+  q.conjA = p.conjB; q.conjB = p.conjA;
+  p = q;
+}
+
+// Stable insertion sort of index groups by the key stride `key`, carrying the other arrays.
+static void sort_groups(int n, int* dim, long long* key, long long* o1, long long* o2) {
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && key[j] < key[j - 1]; --j) {
+      std::swap(dim[j], dim[j - 1]);
+      std::swap(key[j], key[j - 1]);
+      if (o1) std::swap(o1[j], o1[j - 1]);
+      if (o2) std::swap(o2[j], o2[j - 1]);
+    }
+}
+
+static bool operand_shared(const GemmParams& p, int which) {
+  for (int g = 0; g < p.nb; ++g)
+    if ((which == 0 ? p.sAb[g] : p.sBb[g]) != 0) return false;
+  return which == 0 ? (!p.aidx && !p.aoff) : (!p.bidx && !p.boffs);
+}
+
+// A usable in place: row m of batch entry b at (b * M + m) * K, its K entries contiguous.
+static bool dense_a(const GemmParams& p) {
+  if (p.conjA || (p.K & 1) || p.aidx || p.aoff) return false;
+  long long want = 1;
+  for (int g = 0; g < p.nk; ++g) {
+    if (p.sAk[g] != want) return false;
+    want *= p.kdim[g];
+  }
+  for (int g = 0; g < p.nm; ++g) {
+    if (p.sAm[g] != want) return false;
+    want *= p.mdim[g];
+  }
+  if (!operand_shared(p, 0))
+    for (int g = 0; g < p.nb; ++g) {
+      if (p.sAb[g] != want) return false;
+      want *= p.bdim[g];
+    }
+  return (reinterpret_cast<uintptr_t>(p.A) & 15) == 0;
+}
+
+struct TcRole {
+  GemmParams q;
+  bool a_sh, b_sh, ad, ok;
+  double cost;   // bytes written by the operand packing
+};
+
+// Orders the index groups for the tensor-core path: K by the A-side stride, M by
+// the A-side stride when A can be used in place (else by the output stride), N
+// by the output stride (so each thread's 16 columns are, where possible, one
+// contiguous run of the output).
+static TcRole tc_role(const GemmParams& p, long long nbatch, bool swapped) {
+  TcRole r;
+  r.q = p;
+  if (swapped) swap_roles(r.q);
+  GemmParams& q = r.q;
+  sort_groups(q.nk, q.kdim, q.sAk, q.sBk, nullptr);
+  sort_groups(q.nm, q.mdim, q.sAm, q.sCm, nullptr);
+  r.ad = dense_a(q);
+  if (!r.ad) sort_groups(q.nm, q.mdim, q.sCm, q.sAm, nullptr);
+  sort_groups(q.nn, q.ndim, q.sCn, q.sBn, nullptr);
+  r.a_sh = operand_shared(q, 0);
+  r.b_sh = operand_shared(q, 1);
+  r.ok = !(r.a_sh && r.b_sh && nbatch > 1);
+  const double rowsA = (double)(r.a_sh ? 1 : nbatch) * q.M, rowsB = (double)(r.b_sh ? 1 : nbatch) * q.N;
+  r.cost = rowsA * q.K * (r.ad ? 0.0 : 8.0) + rowsB * q.K * 32.0;
+  return r;
+}
+
+// Run the contraction on the tensor cores.  *handled = false (and nothing
+// launched) when the contraction does not fit the kernel.
+static cudaError_t contract_tc(const GemmParams& p0, long long nbatch, cudaStream_t st, ContractTiming* tm,
+                               bool* handled) {
+  *handled = false;
+  if (!tc_available() || p0.M < 1 || p0.N < 1 || p0.K < 1) return cudaSuccess;
+  const TcRole r0 = tc_role(p0, nbatch, false), r1 = tc_role(p0, nbatch, true);
+  if (!r0.ok && !r1.ok) return cudaSuccess;
+  const TcRole& r = (!r0.ok || (r1.ok && r1.cost < r0.cost)) ? r1 : r0;
+  const GemmParams& p = r.q;
+  const bool a_sh = r.a_sh, b_sh = r.b_sh, ad = r.ad;
+  const int Kr = 2 * p.K;
+  const int Kp = (Kr + 31) / 32 * 32;
+  const long long nbA = a_sh ? 1 : nbatch, nbB = b_sh ? 1 : nbatch;
+  const long long rowsA = nbA * p.M, rowsB = nbB * 2LL * p.N;
+  if (rowsA + 128 >= (1LL << 31) || rowsB + 256 >= (1LL << 31)) return cudaSuccess;
+  TcArgs a{};
+  a.e.C = (float2*)p.C;
+  a.e.M = p.M;
+  a.e.N = p.N;
+  a.e.nm = p.nm;
+  a.e.nn = p.nn;
+  a.e.nb = p.nb;
+  for (int g = 0; g < 4; ++g) {
+    a.e.mdim[g] = p.mdim[g]; a.e.ndim[g] = p.ndim[g];
+    a.e.sCm[g] = p.sCm[g]; a.e.sCn[g] = p.sCn[g];
+  }
+  for (int g = 0; g < 2; ++g) { a.e.bdim[g] = p.bdim[g]; a.e.sCb[g] = p.sCb[g]; }
+  a.e.coff = p.coff;
+  a.e.coff_grp = p.coff_grp;
+  a.nbatch = nbatch;
+  a.a_batched = a_sh ? 0 : 1;
+  a.b_batched = b_sh ? 0 : 1;
+  a.merged = (b_sh && !a_sh) ? 1 : 0;
+  a.Kr = Kr;
+  a.err = tc_error_flag();
+  if (!a.err) return cudaSuccess;
+  // scratch: A (unless it is used in place), B hi/lo
+  const long long lda = ad ? Kr : Kp;
+  const size_t a_floats = ad ? 0 : (size_t)rowsA * Kp;
+  const size_t b_floats = (size_t)rowsB * Kp;
+  const size_t b_al = (b_floats + 63) / 64 * 64;
+  float* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * (a_floats + 2 * b_al), st);
+  if (e != cudaSuccess) return e;
+  float* Blo_ = buf;
+  float* Bhi_ = buf + b_al;
+  float* Ahi_ = ad ? (float*)p.A : buf + 2 * b_al;
+  *handled = true;
+  if (!ad) {
+    pack_a_kernel<<<grid_for(rowsA * (Kp / 2)), 256, 0, st>>>(p, nbA, Kp, Ahi_);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    pack_b_kernel<<<grid_for(nbB * (long long)p.N * (Kp / 2)), 256, 0, st>>>(p, nbB, Kp, Bhi_, Blo_);
+    e = cudaGetLastError();
+  }
+  g_launches += ad ? 1 : 2;
+  if (e == cudaSuccess && tm && tm->mma_begin) e = cudaEventRecord(tm->mma_begin, st);
+  TcOperands op{Ahi_, Bhi_, Blo_, lda, (long long)Kp};
+  if (e == cudaSuccess) e = tc_gemm_tf32x3(op, a, st);
+  g_launches++;
+  if (e == cudaSuccess && tm && tm->mma_end) e = cudaEventRecord(tm->mma_end, st);
+  if (tm && e == cudaSuccess) tm->used_tc = true;
+  cudaFreeAsync(buf, st);
+  return e;
+}
+
 // ------------------------------------------------------------------ planner
 namespace {
 struct Lab {
@@ -311,7 +543,7 @@ std::vector<Grp> merge(std::vector<Grp> g, int nops) {
 }  // namespace
 
 cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st, double2 alpha,
-                     double2 beta, double* flops_out) {
+                     double2 beta, double* flops_out, ContractTiming* timing) {
   if (flops_out) *flops_out = 0.0;
   std::vector<Lab> labs;
   auto find = [&](char c) -> Lab& {
@@ -430,6 +662,18 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
   }
   if (p.M == 0 || p.N == 0) return cudaSuccess;
   if (flops_out) *flops_out = 8.0 * (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
+  if (prec == Prec::TF32X3) {
+    // small contractions stay on the SIMT kernel (packing and tile waste dominate)
+    const double macs = (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
+    const bool force = timing && timing->force_tc;
+    if (p.beta_zero && alpha.x == 1.0 && alpha.y == 0.0 && (force || (macs >= 16777216.0 && p.K >= 8))) {
+      bool handled = false;
+      cudaError_t e = contract_tc(p, nbatch, st, timing, &handled);
+      if (handled || e != cudaSuccess) return e;
+    }
+    if (force) return cudaErrorNotSupported;
+    prec = Prec::F32;
+  }
   long long gx = (p.M + 63) / 64;
   int gy = (p.N + 63) / 64;
   if (gx > 2147483647LL || gy > 65535) return cudaErrorInvalidValue;

@@ -13,7 +13,19 @@
 
 namespace tns {
 
-enum class Prec { F64 = 0, F32 = 1, F32_ACC64 = 2 };   // F32_ACC64: float2 inputs, double accumulate + output
+// F32_ACC64: float2 inputs, double accumulate + output.  TF32X3: complex64 on the
+// tensor cores (tcgen05 kind::tf32, three-pass split; FP32-level accuracy) when
+// the contraction is large enough and alpha = 1, beta = 0; SIMT F32 otherwise.
+enum class Prec { F64 = 0, F32 = 1, F32_ACC64 = 2, TF32X3 = 3 };
+
+// Optional timing hooks for the tensor-core path: when the contraction runs on
+// the tensor cores, `mma_begin` / `mma_end` (caller-created events) are recorded
+// around the GEMM kernel (operand packing runs before mma_begin) and used_tc is set.
+struct ContractTiming {
+  cudaEvent_t mma_begin = nullptr, mma_end = nullptr;
+  bool used_tc = false;
+  bool force_tc = false;     // fail with cudaErrorNotSupported instead of falling back (tests)
+};
 
 struct TView {
   void* ptr = nullptr;            // device base pointer (complex elements)
@@ -42,7 +54,7 @@ TView& bcast(TView& v, char label, long long dim);
 // flops_out (optional) receives 8 * M * N * K * batch, the algorithmic real FLOPs.
 cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st,
                      double2 alpha = make_double2(1.0, 0.0), double2 beta = make_double2(0.0, 0.0),
-                     double* flops_out = nullptr);
+                     double* flops_out = nullptr, ContractTiming* timing = nullptr);
 
 // Number of GEMM launches issued so far (for launch accounting).
 long long contract_launches();

@@ -27,20 +27,22 @@ __device__ inline void rr_pair(int r, int i, int np, int& p, int& q) {
 // Rotation J = [[c, s], [-s conj(e), c conj(e)]] on (p, q) that zeroes the (p, q)
 // entry of J^H A J for the Hermitian 2x2 block [[app, apq], [conj(apq), aqq]]
 // (phase-reduce to a real symmetric block, then the symmetric Schur rotation).
-__device__ inline void herm_rot(double app, double aqq, cd apq, double& c, double& s, cd& e) {
-  double ab = sqrt(cabs2(apq));
-  if (!(ab > 1e-300)) {
-    c = 1.0; s = 0.0; e = mk(1.0, 0.0);
+template <typename T, typename C>
+__device__ inline void herm_rot(T app, T aqq, C apq, T& c, T& s, C& e) {
+  const T tiny = sizeof(T) == 8 ? (T)1e-300 : (T)1e-37;
+  T ab = sqrt(cabs2(apq));
+  if (!(ab > tiny)) {
+    c = 1; s = 0; e = mk((T)1, (T)0);
     return;
   }
   e = mk(apq.x / ab, apq.y / ab);
-  double tau = (aqq - app) / (2.0 * ab);
-  double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-  c = 1.0 / hypot(1.0, t);
+  T tau = (aqq - app) / (2 * ab);
+  T t = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + hypot((T)1, tau));
+  c = 1 / hypot((T)1, t);
   s = t * c;
 }
 
-__device__ inline double warp_sum(double v) {
+template <typename T> __device__ inline T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
@@ -49,36 +51,47 @@ __device__ inline double warp_max(double v) {
   return v;
 }
 
+// Precision-dependent Jacobi thresholds: a pair is rotated while
+// |a_pq| > REL * max(|a_pp|, |a_qq|) and |a_pq| > FLOOR * ||A||_F (a few units of
+// rounding: rotating below that level cannot converge).
+template <typename T> struct JacTol;
+template <> struct JacTol<double> { static constexpr double REL = 1e-15, FLOOR = 1e-17; };
+template <> struct JacTol<float> { static constexpr float REL = 3e-7f, FLOOR = 1e-9f; };
+
+// T = double: the FP64 solver.  T = float: the same algorithm in FP32 (complex64
+// input), eigenvalues and eigenvectors written widened to FP64 storage.
+template <typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
-eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long long sV, cd* work, int* status,
-            int use_smem, int* sweeps_out) {
+eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long long sV,
+            typename CplxOf<T>::type* work, int* status, int use_smem, int* sweeps_out) {
+  typedef typename CplxOf<T>::type C;
   extern __shared__ double4 smraw4[];
-  __shared__ double cs_c[256], cs_s[256], cs_d[256];
-  __shared__ cd cs_e[256];
-  __shared__ double red[JAC_THREADS / 32];
-  __shared__ double floor_s;
+  __shared__ T cs_c[256], cs_s[256], cs_d[256];
+  __shared__ C cs_e[256];
+  __shared__ T red[JAC_THREADS / 32];
+  __shared__ T floor_s;
   __shared__ int nrot;
   const int b = blockIdx.x, tid = threadIdx.x;
   const int np = n + (n & 1), half = np / 2;
-  cd* a = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * 2 * np * np;
-  cd* v = a + (long long)np * np;
-  const cd* src = Ain + (long long)b * sA;
-  double tot = 0.0;
+  C* a = use_smem ? reinterpret_cast<C*>(smraw4) : work + (long long)b * 2 * np * np;
+  C* v = a + (long long)np * np;
+  const C* src = Ain + (long long)b * sA;
+  T tot = 0;
   for (int idx = tid; idx < np * np; idx += blockDim.x) {
     int i = idx / np, j = idx % np;
-    cd x = (i < n && j < n) ? src[(long long)i * lda + j] : mk(0.0, 0.0);
-    if (i == j) x.y = 0.0;          // Hermitian: real diagonal
+    C x = (i < n && j < n) ? src[(long long)i * lda + j] : mk((T)0, (T)0);
+    if (i == j) x.y = 0;            // Hermitian: real diagonal
     a[idx] = x;
     tot += cabs2(x);
-    v[idx] = mk(i == j ? 1.0 : 0.0, 0.0);
+    v[idx] = mk(i == j ? (T)1 : (T)0, (T)0);
   }
   tot = warp_sum(tot);
   if ((tid & 31) == 0) red[tid >> 5] = tot;
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
+    T t = 0;
     for (int w = 0; w < JAC_THREADS / 32; ++w) t += red[w];
-    floor_s = 1e-17 * sqrt(t);      // absolute floor below which a pair counts as rotated
+    floor_s = JacTol<T>::FLOOR * sqrt(t);     // absolute floor below which a pair counts as rotated
   }
   __syncthreads();
   bool conv = (np <= 1);
@@ -91,14 +104,14 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
       for (int i = tid; i < half; i += blockDim.x) {
         int p, q;
         rr_pair(r, i, np, p, q);
-        double app = a[p * np + p].x, aqq = a[q * np + q].x;
-        cd apq = a[p * np + q];
-        double ab = sqrt(cabs2(apq));
-        double c = 1.0, s = 0.0, dl = 0.0;
-        cd e = mk(1.0, 0.0);
+        T app = a[p * np + p].x, aqq = a[q * np + q].x;
+        C apq = a[p * np + q];
+        T ab = sqrt(cabs2(apq));
+        T c = 1, s = 0, dl = 0;
+        C e = mk((T)1, (T)0);
         // rounding leaves off-diagonal noise ~ eps * max(|app|, |aqq|): rotating below
-        // that level cannot converge, and leaving it perturbs eigenvectors by ~1e-15
-        if (ab > floor_s && ab > 1e-15 * fmax(fabs(app), fabs(aqq))) {
+        // that level cannot converge, and leaving it perturbs eigenvectors by ~eps
+        if (ab > floor_s && ab > JacTol<T>::REL * fmax(fabs(app), fabs(aqq))) {
           herm_rot(app, aqq, apq, c, s, e);
           dl = (s / c) * ab;        // app' = app - t|apq|, aqq' = aqq + t|apq|
           atomicAdd(&nrot, 1);
@@ -108,40 +121,38 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
       __syncthreads();
       for (int idx = tid; idx < half * np; idx += blockDim.x) {       // rows: J^H A
         int i = idx / np, j = idx % np, p, q;
-        if (cs_s[i] == 0.0) continue;
+        if (cs_s[i] == 0) continue;
         rr_pair(r, i, np, p, q);
-        double c = cs_c[i], s = cs_s[i];
-        cd e = cs_e[i];
-        cd ap = a[p * np + j], aq = a[q * np + j];
-        cd eaq = cmul(e, aq);
+        T c = cs_c[i], s = cs_s[i];
+        C e = cs_e[i];
+        C ap = a[p * np + j], aq = a[q * np + j];
+        C eaq = cmul(e, aq);
         a[p * np + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
         a[q * np + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
       }
       __syncthreads();
       for (int idx = tid; idx < half * np; idx += blockDim.x) {       // columns: (J^H A) J and V J
         int i = idx / np, j = idx % np, p, q;
-        if (cs_s[i] == 0.0) continue;
+        if (cs_s[i] == 0) continue;
         rr_pair(r, i, np, p, q);
-        double c = cs_c[i], s = cs_s[i];
-        cd ec = cconj(cs_e[i]);
-        cd ap = a[j * np + p], aq = a[j * np + q];
-        cd eaq = cmul(ec, aq);
+        T c = cs_c[i], s = cs_s[i];
+        C ec = cconj(cs_e[i]);
+        C ap = a[j * np + p], aq = a[j * np + q];
+        C eaq = cmul(ec, aq);
         a[j * np + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
         a[j * np + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
-        cd vp = v[j * np + p], vq = v[j * np + q];
-        cd evq = cmul(ec, vq);
+        C vp = v[j * np + p], vq = v[j * np + q];
+        C evq = cmul(ec, vq);
         v[j * np + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
         v[j * np + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
       }
       __syncthreads();
       for (int i = tid; i < half; i += blockDim.x) {                   // exact 2x2 result
-        if (cs_s[i] == 0.0) continue;
+        if (cs_s[i] == 0) continue;
         int p, q;
         rr_pair(r, i, np, p, q);
-        double app = a[p * np + p].x, aqq = a[q * np + q].x;
-        (void)app; (void)aqq;
-        a[p * np + q] = mk(0.0, 0.0);
-        a[q * np + p] = mk(0.0, 0.0);
+        a[p * np + q] = mk((T)0, (T)0);
+        a[q * np + p] = mk((T)0, (T)0);
       }
       __syncthreads();
     }
@@ -151,15 +162,15 @@ eigh_kernel(cd* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long l
   if (tid == 0 && status) status[b] = conv ? 0 : 1;
   if (tid == 0 && sweeps_out) sweeps_out[b] = sweeps_done;
   for (int i = tid; i < n; i += blockDim.x) {
-    double li = a[i * np + i].x;
+    T li = a[i * np + i].x;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      double lj = a[j * np + j].x;
+      T lj = a[j * np + j].x;
       if (lj > li || (lj == li && j < i)) ++rank;
     }
-    lam[(long long)b * n + rank] = li;
+    lam[(long long)b * n + rank] = (double)li;
     cd* vo = Vout + (long long)b * sV;
-    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = v[row * np + i];
+    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = to_cd(v[row * np + i]);
   }
 }
 
@@ -276,35 +287,37 @@ svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout
 // the columns of L^{-1} (one thread per column).  Used so that Y W has
 // orthonormal columns when G = Y^H Y; the shift keeps it well defined for
 // rank-deficient Y and damps directions below shift * max G_ii smoothly.
-template <typename C, typename GIN>
+template <typename C, typename GIN, typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
-chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, cd* work, int use_smem) {
+chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::type* work, int use_smem) {
+  typedef typename CplxOf<T>::type CT;
   extern __shared__ double4 smraw4[];
-  __shared__ double red[JAC_THREADS / 32];
-  __shared__ double sh_s;
+  __shared__ T red[JAC_THREADS / 32];
+  __shared__ T sh_s;
   const int b = blockIdx.x, tid = threadIdx.x;
-  cd* L = use_smem ? reinterpret_cast<cd*>(smraw4) : work + (long long)b * 2 * n * n;
-  cd* X = L + (long long)n * n;
+  CT* L = use_smem ? reinterpret_cast<CT*>(smraw4) : work + (long long)b * 2 * n * n;
+  CT* X = L + (long long)n * n;
   const GIN* G = Gin + (long long)b * n * n;
-  double mx = 0.0;
+  T mx = 0;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     int i = idx / n, j = idx % n;
-    cd g = to_cd(G[idx]);
-    L[idx] = (j <= i) ? g : mk(0.0, 0.0);
+    const GIN gi = G[idx];
+    CT g = mk((T)gi.x, (T)gi.y);
+    L[idx] = (j <= i) ? g : mk((T)0, (T)0);
     if (i == j) mx = fmax(mx, g.x);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0) red[tid >> 5] = mx;
   __syncthreads();
   if (tid == 0) {
-    double m = 0.0;
+    T m = 0;
     for (int w = 0; w < JAC_THREADS / 32; ++w) m = fmax(m, red[w]);
-    sh_s = shift * m;
+    sh_s = (T)shift * m;
   }
   __syncthreads();
-  const double sft = sh_s;
+  const T sft = sh_s;
   C* W = Wout + (long long)b * n * n;
-  if (!(sft > 0.0)) {              // Y = 0: no directions
+  if (!(sft > 0)) {                // Y = 0: no directions
     for (int idx = tid; idx < n * n; idx += blockDim.x) W[idx] = from_cd<C>(mk(0.0, 0.0));
     return;
   }
@@ -312,11 +325,11 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, cd* work, int use_sm
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
-      double d = L[j * n + j].x;
-      L[j * n + j] = mk(sqrt(d > sft * 1e-3 ? d : sft), 0.0);
+      T d = L[j * n + j].x;
+      L[j * n + j] = mk(sqrt(d > sft * (T)1e-3 ? d : sft), (T)0);
     }
     __syncthreads();
-    const double inv = 1.0 / L[j * n + j].x;
+    const T inv = 1 / L[j * n + j].x;
     for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i * n + j] = cscale(L[i * n + j], inv);
     __syncthreads();
     const int m = n - j - 1;
@@ -329,40 +342,41 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, cd* work, int use_sm
   }
   // X = L^{-1}: column c by forward substitution (one thread per column)
   for (int c = tid; c < n; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) X[i * n + c] = mk(0.0, 0.0);
+    for (int i = 0; i < c; ++i) X[i * n + c] = mk((T)0, (T)0);
     for (int i = c; i < n; ++i) {
-      cd acc = mk(i == c ? 1.0 : 0.0, 0.0);
+      CT acc = mk(i == c ? (T)1 : (T)0, (T)0);
       for (int k = c; k < i; ++k) acc = csub(acc, cmul(L[i * n + k], X[k * n + c]));
-      X[i * n + c] = cscale(acc, 1.0 / L[i * n + i].x);
+      X[i * n + c] = cscale(acc, 1 / L[i * n + i].x);
     }
   }
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += blockDim.x) {          // W = X^H
     int i = idx / n, j = idx % n;
-    W[idx] = from_cd<C>(cconj(X[j * n + i]));
+    W[idx] = from_cd<C>(to_cd(cconj(X[j * n + i])));
   }
 }
 
-cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
                            cudaStream_t st) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
-  size_t bytes = (size_t)2 * n * n * sizeof(cd);
+  const bool f32 = !g_f64 && !w_f64;               // complex64 in and out: factorise in FP32
+  size_t bytes = (size_t)2 * n * n * (f32 ? sizeof(cf) : sizeof(cd));
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(chol_w_kernel<cd, cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    cudaFuncSetAttribute(chol_w_kernel<cf, cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    cudaFuncSetAttribute(chol_w_kernel<cf, cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cd, cd, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cf, cd, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(chol_w_kernel<cf, cf, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
     attr = true;
   }
   const size_t sm = use_smem ? bytes : 0;
   if (w_f64 && g_f64)
-    chol_w_kernel<cd, cd><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, work, use_smem);
+    chol_w_kernel<cd, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, (cd*)work, use_smem);
   else if (g_f64)
-    chol_w_kernel<cf, cd><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cf*)W, work, use_smem);
-  else if (!w_f64)
-    chol_w_kernel<cf, cf><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, work, use_smem);
+    chol_w_kernel<cf, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cf*)W, (cd*)work, use_smem);
+  else if (f32)
+    chol_w_kernel<cf, cf, float><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, (cf*)work, use_smem);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -380,12 +394,35 @@ cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double*
   if (!use_smem && !work) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(eigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    cudaFuncSetAttribute(eigh_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
     attr = true;
   }
-  eigh_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status, use_smem,
-                                                                sweeps_out);
+  eigh_kernel<double><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
+                                                                        use_smem, sweeps_out);
   return cudaGetLastError();
+}
+
+cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV,
+                             cf* work, int* status, cudaStream_t st, int* sweeps_out) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  if (n > 512) return cudaErrorInvalidValue;
+  int np = n + (n & 1);
+  size_t bytes = (size_t)2 * np * np * sizeof(cf);
+  int use_smem = bytes <= SMEM_LIMIT;
+  if (!use_smem && !work) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(eigh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+    attr = true;
+  }
+  eigh_kernel<float><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
+                                                                       use_smem, sweeps_out);
+  return cudaGetLastError();
+}
+
+bool jacobi_fits_smem_f32(int n) {
+  size_t np = n + (n & 1);
+  return (size_t)2 * np * np * sizeof(cf) <= SMEM_LIMIT;
 }
 
 cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, double* sigma, cd* U, long long sU,

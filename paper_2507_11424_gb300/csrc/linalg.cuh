@@ -16,12 +16,20 @@ namespace tns {
 cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV,
                          cd* work, int* status, cudaStream_t st, int* sweeps_out = nullptr);
 
+// The same solver in FP32 for a complex64 input (the mixed-precision truncation):
+// thresholds scaled to FP32 rounding; lam and V written as float64 / complex128.
+// work: >= batch * 2 * np * np complex64 when !jacobi_fits_smem_f32(n).
+cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV,
+                             cf* work, int* status, cudaStream_t st, int* sweeps_out = nullptr);
+bool jacobi_fits_smem_f32(int n);
+
 // Orthonormalising map from a Gram matrix: W = L^{-H} with
-// L L^H = G + shift * max_i G_ii * I, batched n x n (contiguous); W written as
-// complex128 (w_f64) or complex64.  work: >= batch * 2 n^2 complex when
-// !chol_fits_smem(n).
-// G is complex128 (g_f64) or complex64; the factorisation always runs in FP64.
-cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, cd* work,
+// L L^H = G + shift * max_i G_ii * I, batched n x n (contiguous).  G complex128
+// (g_f64) or complex64, W complex128 (w_f64) or complex64.  The factorisation runs
+// in FP64 unless both are complex64 (the mixed path's shifted CholeskyQR passes),
+// then in FP32.  work: >= batch * 2 n^2 complex of the factorisation's precision
+// when !chol_fits_smem(n).
+cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
                            cudaStream_t st);
 bool chol_fits_smem(int n);
 

@@ -54,10 +54,6 @@ __global__ void omega_kernel(C* out, int n, int kk, uint64_t seed, int stage, in
   }
 }
 
-__global__ void widen_kernel(const cf* in, cd* out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = make_double2(in[i].x, in[i].y);
-}
 
 // UBt[b][i][r] = UB[b][i][r] for r < Rk (first Rk eigenvectors, descending).
 template <typename C> __global__ void take_cols_kernel(const cd* UB, int n, int Rk, C* out, int batch) {
@@ -239,14 +235,55 @@ __global__ void amp_final_kernel(const C* const* sites, int W, long long S, doub
 }
 
 // ------------------------------------------------------------------ host side
-enum ProfClass { PC_ENV = 0, PC_SWEEP = 1, PC_ZIP = 2, PC_EIGH = 3, PC_MARG = 4, PC_PREP = 5 };
+enum ProfClass {
+  PC_ENV = 0, PC_SWEEP = 1, PC_ZIP = 2, PC_EIGH = 3, PC_MARG = 4,
+  PC_PREP = 5, PC_PREP_SWEEP = 6, PC_PREP_ZIP = 7,    // tensor-core operand packing per contraction class
+  PC_ZIP_SIMT = 8, PC_SWEEP_SIMT = 9                  // zip / sweep contractions that ran on the CUDA cores
+};
 
 // contract() bracketed by the state's profiler (no-op when profiling is off).
+// Th[b][n][m] = conj(T[b][m][n]) through 32 x 32 shared-memory tiles (both sides coalesced).
+template <typename C>
+__global__ void transpose_conj_kernel(const C* __restrict__ T, C* __restrict__ Th, long long M, long long N) {
+  __shared__ C tile[32][33];
+  const long long b = blockIdx.z;
+  const long long m0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
+  const C* src = T + b * M * N;
+  C* dst = Th + b * M * N;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long m = m0 + r, n = n0 + threadIdx.x;
+    if (m < M && n < N) tile[r][threadIdx.x] = src[m * N + n];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long n = n0 + r, m = m0 + threadIdx.x;
+    if (m < M && n < N) dst[n * M + m] = cconj(tile[threadIdx.x][r]);
+  }
+}
+
 static cudaError_t pcontract(tns_state* s, int cls, const TView& A, const TView& B, const TView& C, Prec p) {
   cudaEvent_t ev = s->prof.begin(s->st);
   double fl = 0.0;
-  cudaError_t e = contract(A, B, C, p, s->st, make_double2(1.0, 0.0), make_double2(0.0, 0.0), &fl);
-  s->prof.end(cls, ev, fl, s->st);
+  ContractTiming tm;
+  if (ev && p == Prec::TF32X3 &&
+      (cudaEventCreate(&tm.mma_begin) != cudaSuccess || cudaEventCreate(&tm.mma_end) != cudaSuccess)) {
+    if (tm.mma_begin) cudaEventDestroy(tm.mma_begin);
+    tm.mma_begin = tm.mma_end = nullptr;
+  }
+  cudaError_t e = contract(A, B, C, p, s->st, make_double2(1.0, 0.0), make_double2(0.0, 0.0), &fl, &tm);
+  if (tm.used_tc && ev) {
+    // operand packing counts as tensor-core preparation, the GEMM kernel as the class
+    const int prep = cls == PC_ENV ? PC_PREP : (cls == PC_SWEEP ? PC_PREP_SWEEP : PC_PREP_ZIP);
+    s->prof.span(prep, ev, tm.mma_begin, 0.0, true, false);
+    s->prof.span(cls, tm.mma_begin, tm.mma_end, fl, true, true);
+  } else {
+    if (tm.mma_begin) cudaEventDestroy(tm.mma_begin);
+    if (tm.mma_end) cudaEventDestroy(tm.mma_end);
+    int c = cls;
+    if (p == Prec::TF32X3 && cls == PC_ZIP) c = PC_ZIP_SIMT;
+    if (p == Prec::TF32X3 && cls == PC_SWEEP) c = PC_SWEEP_SIMT;
+    s->prof.end(c, ev, fl, s->st);
+  }
   return e;
 }
 
@@ -267,47 +304,6 @@ struct Ctx {
   int R;
 
 };
-
-static long long label_stride(const TView& v, char l) {
-  for (size_t i = 0; i < v.labels.size(); ++i)
-    if (v.labels[i] == l) return v.stride[i];
-  return 0;
-}
-
-// Environment contraction C[M][(n1,n2)] = sum_{(k1,k2)} A[M][(k1,k2)] E[...] on the
-// tensor cores (mixed path): A contiguous M x K complex64, E read through the
-// labels (n1, n2, k1, k2).  Returns false when the shape is not supported.
-struct TcBufs {
-  float *Alo, *Bhi, *Blo;
-  int* err;
-};
-static bool tc_env(tns_state* s, cudaStream_t st, const TcBufs& tb, void* A, long long M, const TView& E, char n1,
-                   char n2, char k1, char k2, void* Cout, cudaError_t* e_out) {
-  long long dn1 = 1, dn2 = 1, dk1 = 1, dk2 = 1;
-  for (size_t i = 0; i < E.labels.size(); ++i) {
-    char c = E.labels[i];
-    if (c == n1) dn1 = E.dim[i];
-    if (c == n2) dn2 = E.dim[i];
-    if (c == k1) dk1 = E.dim[i];
-    if (c == k2) dk2 = E.dim[i];
-  }
-  const long long N = dn1 * dn2, K = dk1 * dk2;
-  const int Kr = (int)(2 * K), Nr = (int)(2 * N);
-  if (!tc_gemm_supported(M, Nr, Kr, Kr, Kr, Nr)) return false;
-  cudaEvent_t ev = s->prof.begin(st);
-  cudaError_t e = tf32_lo((const float*)A, tb.Alo, M * Kr, st);
-  if (e == cudaSuccess)
-    e = expand_b(E.ptr, (int)dn1, (int)dn2, label_stride(E, n1), label_stride(E, n2), (int)dk1, (int)dk2,
-                 label_stride(E, k1), label_stride(E, k2), tb.Bhi, tb.Blo, st);
-  s->prof.end(PC_PREP, ev, 0.0, st);
-  ev = s->prof.begin(st);
-  if (e == cudaSuccess) e = tc_gemm_tf32x3((const float*)A, tb.Alo, M, Kr, Kr, tb.Bhi, tb.Blo, Nr, Kr, (float*)Cout, Nr,
-                                           tb.err, st);
-  s->prof.end(PC_ENV, ev, 8.0 * (double)M * (double)N * (double)K, st);
-  s->launches += 3;
-  *e_out = e;
-  return true;
-}
 
 template <typename F> static void dispatch(bool f64, F&& f) {
   if (f64) f((cd*)nullptr);
@@ -443,8 +439,10 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
 // range finder with one subspace iteration, orthonormalising after every
 // application (Halko, Martinsson, Tropp 2011, Alg. 4.4):
 //   Y0 = T Omega, Q0 = orth(Y0), Z = orth(T^H Q0), Y = T Z, Q = orth(Y),
-// then the truncated SVD of B = Q^H T from the FP64 eigendecomposition of B B^H:
-//   K = Q U_B[:, :R] (column phases fixed), C = K^H T.
+// then the truncated SVD of B = Q^H T from the eigendecomposition of B B^H (FP64
+// path: FP64; mixed path: FP32, the precision B carries):
+//   K = Q U_B[:, :R] (column phases fixed), C = K^H T (returned conjugate-transposed).
+// The products that contract over M read T^H from one transposed copy.
 // With k = R + 8 >= N the test matrix is the identity and Y = T.
 static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long N, int stage, int row, int site,
                            void* Kout, void* Cout, int* Rk_out) {
@@ -458,6 +456,15 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   TNS_TRY(wsget(s, "z_Z", cx.esz * S * N * kk, &Z));
   TNS_TRY(wsget(s, "z_B", cx.esz * S * N * kk, &B));
   TNS_TRY(wsget(s, "z_UBt", cx.esz * S * kk * kk, &UBt));
+  // Th = T^H (per batch entry), read in place by the three products that contract over M
+  void* Th;
+  TNS_TRY(wsget(s, "z_Th", cx.esz * S * M * N, &Th));
+  dispatch(cx.f64, [&](auto* tp) {
+    using C = std::remove_pointer_t<decltype(tp)>;
+    dim3 g((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)S);
+    transpose_conj_kernel<C><<<g, dim3(32, 8), 0, cx.st>>>((const C*)T, (C*)Th, M, N);
+  });
+  s->launches++;
   void* Ymat = Y;
   if (kk == N) {
     Ymat = T;  // test matrix = identity: the range of T is captured exactly
@@ -471,15 +478,16 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}),
                            cx.gp));
     TNS_TRY(orth(cx, Y, S, M, kk, Q));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}, true), view(Q, "Sme", {S, M, kk}),
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Q, "Sme", {S, M, kk}),
                            view(Z, "Sne", {S, N, kk}), cx.gp));
     TNS_TRY(orth(cx, Z, S, N, kk, B));
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(B, "Sne", {S, N, kk}),
                            view(Y, "Sme", {S, M, kk}), cx.gp));
   }
   TNS_TRY(orth(cx, Ymat, S, M, kk, Q));
-  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Q, "Sme", {S, M, kk}, true), view(T, "Smn", {S, M, N}),
-                         view(B, "Sen", {S, kk, N}), cx.gp));
+  // Bt = T^H Q = conj(B)^T with B = Q^H T; read T^H in place from Th
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Q, "Sme", {S, M, kk}),
+                         view(B, "Sne", {S, N, kk}), cx.gp));
   cd *Hm, *V;
   double* mu;
   int* status;
@@ -487,24 +495,27 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   TNS_TRY(wsget(s, "z_V2", sizeof(cd) * S * kk * kk, (void**)&V));
   TNS_TRY(wsget(s, "z_mu", sizeof(double) * S * kk, (void**)&mu));
   TNS_TRY(wsget(s, "z_status2", sizeof(int) * S, (void**)&status));
-  // B B^H: FP64 in the FP64 path; FP32 in the mixed path, widened for the FP64 eigensolver
+  // B B^H and its eigendecomposition: FP64 in the FP64 path; FP32 (the precision B
+  // carries) in the mixed path
+  const long long np = kk + (kk & 1);
   if (cx.f64) {
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sne", {S, N, kk}, true), view(B, "Snf", {S, N, kk}),
                            view(Hm, "Sef", {S, kk, kk}), cx.gp));
+    cd* work = nullptr;
+    if (!jacobi_fits_smem(kk, kk)) TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
+    TNS_TRY_CUDA(peigh(s, Hm, kk, (int)S, mu, V, work, status));
   } else {
     void* H32;
     TNS_TRY(wsget(s, "z_H32", sizeof(cf) * S * kk * kk, &H32));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sen", {S, kk, N}), view(B, "Sfn", {S, kk, N}, true),
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sne", {S, N, kk}, true), view(B, "Snf", {S, N, kk}),
                            view(H32, "Sef", {S, kk, kk}), cx.gp));
-    widen_kernel<<<nblk(S * kk * kk), 256, 0, cx.st>>>((const cf*)H32, Hm, S * kk * kk);
+    cf* work = nullptr;
+    if (!jacobi_fits_smem_f32(kk)) TNS_TRY(wsget(s, "z_jwork32", sizeof(cf) * S * 2 * np * np, (void**)&work));
+    cudaEvent_t ev = s->prof.begin(s->st);
+    TNS_TRY_CUDA(eigh_batched_f32((const cf*)H32, kk * kk, kk, kk, (int)S, mu, V, kk * kk, work, status, s->st));
+    s->prof.end(PC_EIGH, ev, 0.0, s->st);
     s->launches++;
   }
-  cd* work = nullptr;
-  if (!jacobi_fits_smem(kk, kk)) {
-    long long np = kk + (kk & 1);
-    TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
-  }
-  TNS_TRY_CUDA(peigh(s, Hm, kk, (int)S, mu, V, work, status));
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     take_cols_kernel<C><<<nblk(S * kk * Rk), 256, 0, cx.st>>>(V, kk, Rk, (C*)UBt, (int)S);
@@ -515,8 +526,9 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     using C = std::remove_pointer_t<decltype(tp)>;
     phase_fix_kernel<C><<<dim3(Rk, (unsigned)S), 128, 0, cx.st>>>((C*)Kout, (int)M, Rk);
   });
-  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Kout, "Smr", {S, M, Rk}, true), view(T, "Smn", {S, M, N}),
-                         view(Cout, "Srn", {S, Rk, N}), cx.gp));
+  // C = K^H T, stored conjugate-transposed: Cout[S][n][r] = conj(C[r][n]) = (T^H K)[n][r]
+  TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Kout, "Smr", {S, M, Rk}),
+                         view(Cout, "Snr", {S, N, Rk}), cx.gp));
   s->launches += 2;
   return TNS_OK;
 }
@@ -559,16 +571,15 @@ static tns_status zip(Ctx& cx, ZipSpec& zs) {
       set_error("zip: bond mismatch at site %d (a %lld/%lld, l %lld/%lld)", j, a, a_prev, l, l_prev);
       return TNS_ERR_STATE;
     }
-    // X[S][k][l][Pm][b] = sum_a C[S][k][a][l] m[S][a][Pm][b]
-    std::vector<long long> xd = {S, kprev, l};
-    std::string xl = "Skl";
-    long long xsz = kprev * l;
+    // X[S][k][b][l][Pm] = sum_a C[S][k][a][l] m[S][a][Pm][b]  (rows (k,b), contiguous (l,Pm): the
+    // next contraction reads X in place)
+    std::vector<long long> xd = {S, kprev, bdm, l};
+    std::string xl = "Skbl";
+    long long xsz = kprev * bdm * l;
     for (char c : Pm) { xl.push_back(c); long long d = vdim(mv, c); xd.push_back(d); xsz *= d; }
-    xl.push_back('b');
-    xd.push_back(bdm);
-    xsz *= bdm;
     TNS_TRY(wsget(s, "zip_X", cx.esz * S * xsz, &X));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Cp, "Skal", {S, kprev, a, l}), mv, view(X, xl, xd), cx.gp));
+    // C is held conjugate-transposed ([S][a][l][k] = conj C[k][a][l]), see truncate()
+    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Cp, "Salk", {S, a, l, kprev}, true), mv, view(X, xl, xd), cx.gp));
     // T[S][k][out][b][r] = sum_{l, Pc} X w
     std::vector<long long> td = {S, kprev};
     std::string tl = "Sk";
@@ -723,17 +734,32 @@ static tns_status make_ctx(tns_state* s, int chi_b, uint64_t seed, Ctx& cx) {
   cx.s = s;
   cx.st = s->st;
   cx.f64 = (s->prec == TNS_PREC_FP64);
-  cx.gp = cx.f64 ? Prec::F64 : Prec::F32;
+  cx.gp = cx.f64 ? Prec::F64 : (s->tensor_cores ? Prec::TF32X3 : Prec::F32);
   cx.esz = cx.f64 ? sizeof(cd) : sizeof(cf);
   cx.seed = seed;
   cx.R = chi_b;
   return ensure_work_cells(s, cx.f64);
 }
 
+// Reads and clears the tensor-core timeout flag (stream already synchronised).
+static tns_status check_tc_error(const Ctx& cx) {
+  if (cx.gp != Prec::TF32X3) return TNS_OK;
+  int* f = tc_error_flag();
+  if (!f) return TNS_OK;
+  int h = 0;
+  TNS_TRY_CUDA(cudaMemcpy(&h, f, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return TNS_OK;
+  TNS_TRY_CUDA(cudaMemset(f, 0, sizeof(int)));
+  set_error("tensor-core GEMM pipeline wait timed out");
+  return TNS_ERR_NUMERIC;
+}
+
 tns_status log_norm(tns_state* s, int chi_b, double* out) {
   Ctx cx;
   TNS_TRY(make_ctx(s, chi_b, 0, cx));
   TNS_TRY(build_envs(cx));
+  TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  TNS_TRY(check_tc_error(cx));
   *out = s->env.log_norm;
   return TNS_OK;
 }
@@ -763,6 +789,7 @@ static long long sampler_bytes_per_sample(tns_state* s, const Ctx& cx) {
   long long site = R * 2 * chi * R;                      // K' site
   long long per = 2 * big + Tm + 2 * R * 2 * chi * kk + 2 * R * chi * kk + s->W * site * 2 + s->W * R * rho * R +
                   3 * R * rho * R + 2 * R * chi * R * s->W + R * 4096 * 2 + R * chi * chi * R;
+  if (cx.gp == Prec::TF32X3) per += 2 * Tm;            // tensor-core operand packing
   return per * (long long)cx.esz + 64 * kk * kk * 16;
 }
 
@@ -809,16 +836,6 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   TNS_TRY(wsget(s, "s_G", cx.esz * chunk * 2 * F_cap, &Gb));
   TNS_TRY(wsget(s, "s_bigA", cx.esz * chunk * big_cap, &bigA));
   TNS_TRY(wsget(s, "s_bigB", cx.esz * chunk * big_cap, &bigB));
-  const bool use_tc = !cx.f64 && s->tensor_cores;
-  TcBufs tb{nullptr, nullptr, nullptr, nullptr};
-  if (use_tc) {
-    const long long kmax = R * chimax;                      // K, N <= R * chi
-    TNS_TRY(wsget(s, "s_tc_Alo", cx.esz * chunk * big_cap, (void**)&tb.Alo));
-    TNS_TRY(wsget(s, "s_tc_Bhi", sizeof(float) * 4 * kmax * kmax, (void**)&tb.Bhi));
-    TNS_TRY(wsget(s, "s_tc_Blo", sizeof(float) * 4 * kmax * kmax, (void**)&tb.Blo));
-    TNS_TRY(wsget(s, "s_tc_err", sizeof(int), (void**)&tb.err));
-    TNS_TRY_CUDA(cudaMemsetAsync(tb.err, 0, sizeof(int), cx.st));
-  }
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     fill_kernel<C><<<nblk(chunk), 256, 0, cx.st>>>((C*)ones, chunk, 1.0);
@@ -877,14 +894,11 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         if (j + 1 == W) Fv.stride[0] = 0;
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, Kview(j, 'a', 's', 'd', 'A', Sz, false), Fv,
                               view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), cx.gp));
-        // R2: T2[S][a][s][B][e][D] = sum_{d,f} T1 E[e,d,D,f]
-        cudaError_t ge = cudaSuccess;
-        if (!(use_tc && tc_env(s, cx.st, tb, bigA, Sz * ka * P * kb, Ev, 'e', 'D', 'd', 'f', bigB, &ge)))
-          ge = pcontract(s, PC_ENV, view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
-                         view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), cx.gp);
-        TNS_TRY_CUDA(ge);
-        // R3: F_j[S][a][e][c] = sum_{s,D,B} T2 conj K'[c,s,D,B]
-        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SasBeD", {Sz, ka, P, kb, re, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
+        // R2: T2[S][a][e][s][B][D] = sum_{d,f} T1 E[e,d,D,f]  (rows (a,e) of T2 are the next step's K-contiguous rows)
+        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "SasBdf", {Sz, ka, P, kb, Dd, rf}), Ev,
+                               view(bigB, "SaesBD", {Sz, ka, re, P, kb, Dd}), cx.gp));
+        // R3: F_j[S][a][e][c] = sum_{s,B,D} T2 conj K'[c,s,D,B]
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SaesBD", {Sz, ka, re, P, kb, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
                               view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp));
         dispatch(cx.f64, [&](auto* tp) {
           using C = std::remove_pointer_t<decltype(tp)>;
@@ -912,14 +926,11 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         // L1: U1[S][c][s][A][e][d] = sum_a L[a,e,c] K'[a,s,d,A]
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(Lc, "Saec", {S, ka, re, ka}), Kview(j, 'a', 's', 'd', 'A', S, false),
                               view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), cx.gp));
-        // L2: U2[S][c][s][A][D][f] = sum_{e,d} U1 E[e,d,D,f]
-        cudaError_t ge = cudaSuccess;
-        if (!(use_tc && tc_env(s, cx.st, tb, bigA, S * ka * P * kb, Ev, 'D', 'f', 'e', 'd', bigB, &ge)))
-          ge = pcontract(s, PC_ENV, view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
-                         view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), cx.gp);
-        TNS_TRY_CUDA(ge);
+        // L2: U2[S][s][A][f][c][D] = sum_{e,d} U1 E[e,d,D,f]  (rows (A,f) of U2 are the next step's K-contiguous rows)
+        TNS_TRY_CUDA(pcontract(s, PC_ENV, view(bigA, "ScsAed", {S, ka, P, kb, re, Dd}), Ev,
+                               view(bigB, "SsAfcD", {S, P, kb, rf, ka, Dd}), cx.gp));
         // L3: G[S][s][A][f][B] = sum_{c,D} U2 conj K'[c,s,D,B]
-        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "ScsADf", {S, ka, P, kb, Dd, rf}), Kview(j, 'c', 's', 'D', 'B', S, true),
+        TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SsAfcD", {S, P, kb, rf, ka, Dd}), Kview(j, 'c', 's', 'D', 'B', S, true),
                               view(Gb, "SsAfB", {S, P, kb, rf, kb}), cx.gp));
         const int c = rev ? W - 1 - j : j;
         const int q = s->cell[s->cidx(b, c)].qubit;
@@ -944,12 +955,7 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
   s->prof.resolve();
-  if (use_tc) {
-    int herr = 0;
-    TNS_TRY_CUDA(cudaMemcpy(&herr, tb.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) { set_error("tensor-core GEMM pipeline wait timed out"); return TNS_ERR_NUMERIC; }
-  }
-  return TNS_OK;
+  return check_tc_error(cx);
 }
 
 tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase) {
@@ -1043,7 +1049,7 @@ tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, 
     s->launches++;
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
-  return TNS_OK;
+  return check_tc_error(cx);
 }
 
 }  // namespace tns

@@ -43,15 +43,17 @@ struct StoredMPS {
 
 // Event-bracketed timing of kernel classes (see tns_profile_enable).
 struct Profiler {
-  static constexpr int NCLASS = 6;
+  static constexpr int NCLASS = 10;
   bool on = false;
-  struct Rec { int cls; cudaEvent_t a, b; double flops; };
+  struct Rec { int cls; cudaEvent_t a, b; double flops; bool own_a = true, own_b = true; };
   std::vector<Rec> pending;
-  double ms[NCLASS] = {0, 0, 0, 0, 0, 0};
-  double flops[NCLASS] = {0, 0, 0, 0, 0, 0};
-  long long n[NCLASS] = {0, 0, 0, 0, 0, 0};
+  double ms[NCLASS] = {};
+  double flops[NCLASS] = {};
+  long long n[NCLASS] = {};
   cudaEvent_t begin(cudaStream_t st);
   void end(int cls, cudaEvent_t a, double fl, cudaStream_t st);
+  // Record the interval between two already-recorded events; own_* = destroy the event when resolved.
+  void span(int cls, cudaEvent_t a, cudaEvent_t b, double fl, bool own_a, bool own_b);
   void resolve();   // after the stream is synchronised
   void clear();
 };

@@ -1,22 +1,28 @@
-// Tensor-core (tcgen05) complex contraction for the environment GEMMs of the
-// marginal sweeps, C = A B^T with A: M x K complex, B: N x K complex (both
-// K-contiguous), C: M x N complex, all complex64.
+// Tensor-core (tcgen05) batched complex GEMM, C[b] = A[b] B[b]^T, used by every
+// mixed-precision contraction of the sampler whose shape fits (the planner in
+// contract.cu packs the operands and describes the output layout).
 //
 // Complex arithmetic runs as one real GEMM: A is read as M x 2K real (interleaved
-// re/im), B is expanded once into the 2N x 2K real block matrix
+// re/im), B is expanded into the 2N x 2K real block matrix
 //   [ Br  -Bi ]   rows 2n   (real part of column n)
 //   [ Bi   Br ]   rows 2n+1 (imaginary part)
 // interleaved by k, so C comes out interleaved.  Precision: kind::tf32 with a
-// three-pass split product A_hi B_hi + A_hi B_lo + A_lo B_hi, where the hi part
-// is the FP32 value itself (the tensor core reads its top 19 bits) and the lo
-// part the exact FP32 remainder; all passes accumulate in one FP32 TMEM tile.
+// three-pass split product A_hi B_hi + A_hi B_lo + A_lo B_hi, where hi is the
+// value rounded to the nearest TF32 (10 explicit mantissa bits) and lo the
+// remainder rounded the same way (|lo| <= 2^-11 |x|); each real product is then
+// within 3 * 2^-22 |a||b| (the dropped lo*lo term and the two lo roundings), and
+// all products accumulate in one FP32 TMEM tile.
 //
-// Kernel: one 128 x 256 output tile per CTA, 128 threads.  Thread 0 issues TMA
-// loads (128B-swizzled, 32 FP32 of K per row) into a 4-stage ring guarded by
-// mbarriers; thread 32 issues tcgen05.mma (M=128, N=256, K=8 per instruction)
-// and releases each stage with tcgen05.commit; all four warps then read the
-// accumulator from TMEM (each warp its 32 lanes) and store it.  Every wait has
-// a 1 s time limit after which the kernel raises an error flag and exits.
+// Kernel: one 128 x BN output tile per CTA (BN = 128 or 256 real columns), 128
+// threads.  Thread 0 issues TMA loads (128B-swizzled, 32 FP32 of K per row) of
+// A, B_hi and B_lo into a ring of 2 (BN = 256) or 3 (BN = 128) stages guarded by
+// mbarriers; warps 2-3 derive A_lo from the staged A tile in shared memory (no
+// HBM pass over A); thread 32 issues the three tcgen05.mma products per k-step
+// (M=128, N=BN, K=8 per instruction) and releases each stage with
+// tcgen05.commit; all four warps then read the accumulator from TMEM (each warp
+// its 32 lanes) and store it through the output's index decomposition (runs of
+// 16 contiguous complex outputs as 16-byte vector stores).  Every wait has a 1 s
+// time limit after which the kernel raises an error flag and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -29,11 +35,13 @@
 namespace tns {
 
 namespace {
-constexpr int BM = 128, BN = 256, BKF = 32, STAGES = 4;
-constexpr int TMEM_COLS = 256;
+constexpr int BM = 128, BKF = 32;
 constexpr size_t TILE_A = (size_t)BM * BKF * sizeof(float);   // 16 KB
-constexpr size_t TILE_B = (size_t)BN * BKF * sizeof(float);   // 32 KB
-constexpr size_t SMEM_BYTES = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+// pipeline depth: each stage holds A, A_lo, B_hi, B_lo (96 KB at BN = 256, 64 KB at BN = 128)
+template <int BN> struct Stages { static constexpr int value = BN == 256 ? 2 : 3; };
+template <int BN> constexpr size_t smem_bytes() {
+  return Stages<BN>::value * (2 * TILE_A + 2 * (size_t)BN * BKF * sizeof(float)) + 1024 + 256;
+}
 constexpr unsigned long long WAIT_NS = 1000000000ull;          // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -73,6 +81,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
       : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -114,32 +127,77 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 }  // namespace
 
+// Row offset of output row m (decomposed over the epilogue's M groups).
+__device__ __forceinline__ long long tc_row_off(const TcEpilogue& e, long long m) {
+  long long o = 0;
+  for (int g = 0; g < e.nm; ++g) {
+    o += (m % e.mdim[g]) * e.sCm[g];
+    m /= e.mdim[g];
+  }
+  return o;
+}
+__device__ __forceinline__ long long tc_batch_off(const TcEpilogue& e, long long b) {
+  long long o = 0;
+  int bi[2] = {0, 0};
+  for (int g = 0; g < e.nb; ++g) {
+    bi[g] = (int)(b % e.bdim[g]);
+    b /= e.bdim[g];
+    o += bi[g] * e.sCb[g];
+  }
+  if (e.coff) o += e.coff[bi[e.coff_grp]];
+  return o;
+}
+
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
-tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mAlo,
-                      const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, float* C,
-                      long long ldc, long long M, int Nr, int Kr, int* err) {
+tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBhi,
+                      const __grid_constant__ CUtensorMap mBlo, const TcArgs p) {
+  constexpr int STAGES = Stages<BN>::value;
+  constexpr size_t TILE_B = (size_t)BN * BKF * sizeof(float);
+  constexpr int NC = BN / 2;                       // complex columns per tile
   extern __shared__ unsigned char smem_raw[];
+  __shared__ long long colC[NC];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
-  float* sA = reinterpret_cast<float*>(base);
-  float* sB = sA + STAGES * BM * BKF;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * BN * BKF);
-  uint64_t* empty = full + STAGES;
+  float* sA = reinterpret_cast<float*>(base);      // [STAGES][BM*BKF]
+  float* sAlo = sA + STAGES * BM * BKF;            // [STAGES][BM*BKF]
+  float* sB = sAlo + STAGES * BM * BKF;            // [STAGES][BN*BKF]
+  float* sBlo = sB + STAGES * BN * BKF;            // [STAGES][BN*BKF]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sBlo + STAGES * BN * BKF);
+  uint64_t* lo_ready = full + STAGES;
+  uint64_t* empty = lo_ready + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // linear grid, N tiles fastest: the CTAs sharing an A row-block run together and
-  // read it from L2 instead of re-reading it from HBM once per N tile
-  const int ntn = (Nr + BN - 1) / BN;
-  const long long m0 = (long long)(blockIdx.x / ntn) * BM;
-  const int n0 = (int)(blockIdx.x % ntn) * BN;
-  const int nkb = (Kr + BKF - 1) / BKF;
-  const int nsteps = 3 * nkb;
+  // linear grid, N tiles fastest, then M tiles, then batch entries: the CTAs sharing
+  // an A row-block run together and read it from L2 instead of HBM once per N tile
+  const long long per_b = (long long)p.tiles_m * p.tiles_n;
+  const long long bz = blockIdx.x / per_b;
+  const long long rem = blockIdx.x % per_b;
+  const long long mt = rem / p.tiles_n;
+  const int nt = (int)(rem % p.tiles_n);
+  const long long m0 = mt * BM;                            // first row of the tile (global in merged mode)
+  const int n0 = nt * BN;                                  // first real column
+  const int a_row0 = (int)((p.merged || !p.a_batched ? 0 : bz * p.e.M) + m0);
+  const int b_row0 = (int)((p.b_batched ? bz * 2LL * p.e.N : 0) + n0);
+  const int nkb = (p.Kr + BKF - 1) / BKF;
 
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) {
+    long long n = n0 / 2 + i, o = -1;
+    if (n < p.e.N) {
+      o = 0;
+      for (int g = 0; g < p.e.nn; ++g) {
+        o += (n % p.e.ndim[g]) * p.e.sCn[g];
+        n /= p.e.ndim[g];
+      }
+    }
+    colC[i] = o;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
+      mbar_init(&lo_ready[s], 64);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
@@ -148,7 +206,7 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     tc_fence_before();
@@ -159,18 +217,16 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   const unsigned long long deadline = gtimer() + WAIT_NS;
 
   if (threadIdx.x == 0) {
-    // producer: TMA loads of (A or A_lo, B_hi or B_lo) per k-step
+    // producer: TMA loads of A, B_hi, B_lo per k-block
     int issued = 0;
-    for (int it = 0; it < nsteps; ++it) {
+    for (int it = 0; it < nkb; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, deadline)) { *abort_flag = 1; break; }
-      const int pass = it / nkb, kb = it % nkb;
-      const CUtensorMap* ma = (pass == 2) ? &mAlo : &mA;
-      const CUtensorMap* mb = (pass == 1) ? &mBlo : &mBhi;
-      mbar_expect_tx(&full[s], (uint32_t)(TILE_A + TILE_B));
-      tma_load_2d(sA + s * BM * BKF, ma, &full[s], kb * BKF, (int)m0);
-      tma_load_2d(sB + s * BN * BKF, mb, &full[s], kb * BKF, n0);
+      mbar_expect_tx(&full[s], (uint32_t)(TILE_A + 2 * TILE_B));
+      tma_load_2d(sA + s * BM * BKF, &mA, &full[s], it * BKF, a_row0);
+      tma_load_2d(sB + s * BN * BKF, &mBhi, &full[s], it * BKF, b_row0);
+      tma_load_2d(sBlo + s * BN * BKF, &mBlo, &full[s], it * BKF, b_row0);
       issued = it + 1;
     }
     if (*abort_flag) {
@@ -180,90 +236,101 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
         mbar_wait(&full[it % STAGES], (it / STAGES) & 1, d2);
     }
   } else if (threadIdx.x == 32) {
-    // MMA issuer
+    // MMA issuer: A B_hi + A B_lo + A_lo B_hi per k-block
     const uint32_t idesc = idesc_tf32(BM, BN);
     bool ok = true;
-    for (int it = 0; it < nsteps; ++it) {
+    for (int it = 0; it < nkb; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
-      if (*abort_flag || !mbar_wait(&full[s], ph, deadline)) { *abort_flag = 1; ok = false; break; }
+      if (*abort_flag || !mbar_wait(&full[s], ph, deadline) || !mbar_wait(&lo_ready[s], ph, deadline)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * BM * BKF), b0 = smem_u32(sB + s * BN * BKF);
+      const uint32_t a0 = smem_u32(sA + s * BM * BKF), al0 = smem_u32(sAlo + s * BM * BKF);
+      const uint32_t b0 = smem_u32(sB + s * BN * BKF), bl0 = smem_u32(sBlo + s * BN * BKF);
 #pragma unroll
-      for (int kk = 0; kk < BKF / 8; ++kk)
+      for (int kk = 0; kk < BKF / 8; ++kk) {
         mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(bl0 + kk * 32), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(al0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, 1u);
+      }
       mma_commit(&empty[s]);
     }
     // always signal `done`: it completes once every MMA issued above has finished,
     // so TMEM is never released under an MMA still in flight
     mma_commit(done);
     if (!ok) *abort_flag = 1;
+  } else if (warp >= 2) {
+    // converters: split the staged A tile in place into hi = tf32_rn(A) and
+    // lo = tf32_rn(A - hi), elementwise, so the swizzled layout carries over unchanged
+    const int t = threadIdx.x - 64;
+    for (int it = 0; it < nkb; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (it / STAGES) & 1;
+      if (*abort_flag || !mbar_wait(&full[s], ph, deadline)) { *abort_flag = 1; break; }
+      float4* hi = reinterpret_cast<float4*>(sA + s * BM * BKF);
+      float4* dst = reinterpret_cast<float4*>(sAlo + s * BM * BKF);
+#pragma unroll 4
+      for (int i = t; i < BM * BKF / 4; i += 64) {
+        const float4 v = hi[i];
+        const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+        hi[i] = h;
+        dst[i] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+      }
+      fence_proxy_async();
+      mbar_arrive(&lo_ready[s]);
+    }
   }
   __syncwarp();
   const bool ready = mbar_wait(done, 0, deadline) && !*abort_flag;
   tc_fence_after();
   if (ready) {
-    const long long row = m0 + warp * 32 + lane;
+    const long long r = m0 + warp * 32 + lane;
+    long long b = bz, m = r;
+    bool valid;
+    if (p.merged) {
+      b = r / p.e.M;
+      m = r % p.e.M;
+      valid = b < p.nbatch;
+    } else {
+      valid = m < p.e.M;
+    }
+    float2* dst = nullptr;
+    if (valid) dst = p.e.C + tc_batch_off(p.e, b) + tc_row_off(p.e, m);
 #pragma unroll 1
     for (int cb = 0; cb < BN; cb += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
-      if (row < M) {
-        float* dst = C + row * ldc + n0 + cb;
-        const int lim = Nr - (n0 + cb);
-        if (lim >= 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (!valid) continue;
+      const int c0 = cb / 2;
+      const long long o0 = colC[c0];
+      bool contig = o0 >= 0;
 #pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<float4*>(dst + j) =
-                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                            __uint_as_float(r[j + 3]));
-        } else {
-          for (int j = 0; j < 32 && j < lim; ++j) dst[j] = __uint_as_float(r[j]);
+      for (int i = 1; i < 16; ++i) contig = contig && (colC[c0 + i] == o0 + i);
+      if (contig && ((reinterpret_cast<uintptr_t>(dst + o0) & 15) == 0)) {
+        float4* d4 = reinterpret_cast<float4*>(dst + o0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          d4[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                              __uint_as_float(v[4 * j + 3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const long long o = colC[c0 + i];
+          if (o >= 0) dst[o] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
         }
       }
     }
-  } else if (threadIdx.x == 0 && err) {
-    atomicExch(err, 1);
+  } else if (threadIdx.x == 0 && p.err) {
+    atomicExch(p.err, 1);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-  }
-}
-
-// lo = x - (x with its low 13 mantissa bits cleared): the part of x a TF32 read drops.
-__global__ void tf32_lo_kernel(const float* __restrict__ x, float* __restrict__ lo, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    float v = x[i];
-    float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-    lo[i] = v - h;
-  }
-}
-
-// Real block expansion of a complex N x K operand read through two sub-indices
-// per dimension: value E[n1*sN1 + n2*sN2 + k1*sK1 + k2*sK2], n = n1*N2 + n2,
-// k = k1*K2 + k2.  Writes hi (the value) and lo (its TF32 remainder).
-__global__ void expand_b_kernel(const float2* __restrict__ E, int N1, int N2, long long sN1, long long sN2, int K1,
-                                int K2, long long sK1, long long sK2, float* __restrict__ Bhi,
-                                float* __restrict__ Blo) {
-  const long long N = (long long)N1 * N2, K = (long long)K1 * K2;
-  const long long Kr = 2 * K;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N * K;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long n = idx / K, k = idx % K;
-    long long n1 = n / N2, n2 = n % N2, k1 = k / K2, k2 = k % K2;
-    float2 v = E[n1 * sN1 + n2 * sN2 + k1 * sK1 + k2 * sK2];
-    float q[4] = {v.x, -v.y, v.y, v.x};
-    long long o[4] = {(2 * n) * Kr + 2 * k, (2 * n) * Kr + 2 * k + 1, (2 * n + 1) * Kr + 2 * k,
-                      (2 * n + 1) * Kr + 2 * k + 1};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float h = __uint_as_float(__float_as_uint(q[t]) & 0xFFFFE000u);
-      Bhi[o[t]] = q[t];
-      Blo[o[t]] = q[t] - h;
-    }
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
   }
 }
 
@@ -281,7 +348,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-static bool make_map(CUtensorMap* map, const float* ptr, long long rows, int cols, long long ld, int box_rows) {
+static bool make_map(CUtensorMap* map, const float* ptr, long long rows, long long cols, long long ld, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -294,47 +361,58 @@ static bool make_map(CUtensorMap* map, const float* ptr, long long rows, int col
   return r == CUDA_SUCCESS;
 }
 
-bool tc_gemm_supported(long long M, int Nr, int Kr, long long lda, long long ldb, long long ldc) {
-  if (!encode_fn()) return false;
-  if (M < 1 || Nr < 1 || Kr < BKF || M >= (1LL << 31)) return false;
-  if ((lda * 4) % 16 || (ldb * 4) % 16 || (ldc % 4) || (Kr % 4)) return false;
-  return true;
-}
+bool tc_available() { return encode_fn() != nullptr; }
 
-cudaError_t tc_gemm_tf32x3(const float* A, const float* Alo, long long M, int Kr, long long lda, const float* Bhi,
-                           const float* Blo, int Nr, long long ldb, float* C, long long ldc, int* err,
-                           cudaStream_t st) {
-  if (!tc_gemm_supported(M, Nr, Kr, lda, ldb, ldc)) return cudaErrorNotSupported;
-  CUtensorMap ma, malo, mbhi, mblo;
-  if (!make_map(&ma, A, M, Kr, lda, BM) || !make_map(&malo, Alo, M, Kr, lda, BM) ||
-      !make_map(&mbhi, Bhi, Nr, Kr, ldb, BN) || !make_map(&mblo, Blo, Nr, Kr, ldb, BN))
+template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArgs& a0, cudaStream_t st) {
+  constexpr size_t SMEM = smem_bytes<BN>();
+  TcArgs a = a0;
+  const long long rowsA = (a.a_batched ? a.nbatch : 1) * a.e.M;
+  const long long rowsB = (a.b_batched ? a.nbatch : 1) * 2LL * a.e.N;
+  if (rowsA + BM >= (1LL << 31) || rowsB + BN >= (1LL << 31)) return cudaErrorNotSupported;
+  if ((op.lda * 4) % 16 || (op.ldb * 4) % 16 || (reinterpret_cast<uintptr_t>(op.A) & 15) ||
+      (reinterpret_cast<uintptr_t>(op.Bhi) & 15) || (reinterpret_cast<uintptr_t>(op.Blo) & 15))
+    return cudaErrorNotSupported;
+  CUtensorMap ma, mbhi, mblo;
+  if (!make_map(&ma, op.A, rowsA, a.Kr, op.lda, BM) || !make_map(&mbhi, op.Bhi, rowsB, a.Kr, op.ldb, BN) ||
+      !make_map(&mblo, op.Blo, rowsB, a.Kr, op.ldb, BN))
     return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long tiles = ((M + BM - 1) / BM) * ((Nr + BN - 1) / BN);
-  if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
-  tc_gemm_tf32x3_kernel<<<(unsigned)tiles, 128, SMEM_BYTES, st>>>(ma, malo, mbhi, mblo, C, ldc, M, Nr, Kr, err);
+  a.tiles_n = (int)((2LL * a.e.N + BN - 1) / BN);
+  const long long mrows = a.merged ? a.nbatch * a.e.M : a.e.M;
+  const long long tm = (mrows + BM - 1) / BM;
+  if (tm >= (1LL << 31)) return cudaErrorNotSupported;
+  a.tiles_m = (int)tm;
+  const long long tiles = tm * a.tiles_n * (a.merged ? 1 : a.nbatch);
+  if (tiles >= (1LL << 31)) return cudaErrorNotSupported;
+  tc_gemm_tf32x3_kernel<BN><<<(unsigned)tiles, 128, SMEM, st>>>(ma, mbhi, mblo, a);
   return cudaGetLastError();
 }
 
-cudaError_t tf32_lo(const float* x, float* lo, long long n, cudaStream_t st) {
-  long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
-  tf32_lo_kernel<<<(unsigned)std::max<long long>(1, blocks), 256, 0, st>>>(x, lo, n);
-  return cudaGetLastError();
+cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st) {
+  if (!tc_available() || a.e.M < 1 || a.e.N < 1 || a.Kr < 1 || a.nbatch < 1) return cudaErrorNotSupported;
+  if (2LL * a.e.N <= 128) return launch_bn<128>(op, a, st);
+  return launch_bn<256>(op, a, st);
 }
 
-cudaError_t expand_b(const void* E, int N1, int N2, long long sN1, long long sN2, int K1, int K2, long long sK1,
-                     long long sK2, float* Bhi, float* Blo, cudaStream_t st) {
-  long long n = (long long)N1 * N2 * K1 * K2;
-  long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
-  expand_b_kernel<<<(unsigned)std::max<long long>(1, blocks), 256, 0, st>>>(
-      static_cast<const float2*>(E), N1, N2, sN1, sN2, K1, K2, sK1, sK2, Bhi, Blo);
-  return cudaGetLastError();
+int* tc_error_flag() {
+  static int* flags[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!flags[dev]) {
+    int* f = nullptr;
+    if (cudaMalloc(&f, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(f, 0, sizeof(int)) != cudaSuccess) { cudaFree(f); return nullptr; }
+    flags[dev] = f;
+  }
+  return flags[dev];
 }
 
 }  // namespace tns

@@ -1,24 +1,68 @@
-// Tensor-core (tcgen05, kind::tf32, three-pass split) complex contraction.  See tc_gemm.cu.
+// Tensor-core (tcgen05, kind::tf32, three-pass split) batched complex GEMM.  See tc_gemm.cu.
 #pragma once
 #include "common.cuh"
+#include <string.h>
 
 namespace tns {
 
-// C[M x Nr] = A[M x Kr] * B[Nr x Kr]^T in real FP32 storage, where A is a complex
-// M x (Kr/2) matrix read as interleaved reals and B the real block expansion of a
-// complex (Nr/2) x (Kr/2) operand (expand_b).  Alo is the TF32 remainder of A
-// (tf32_lo); Bhi/Blo come from expand_b.  Row strides in floats.  err: device int
-// set to 1 if a pipeline wait timed out (results then invalid).
-cudaError_t tc_gemm_tf32x3(const float* A, const float* Alo, long long M, int Kr, long long lda, const float* Bhi,
-                           const float* Blo, int Nr, long long ldb, float* C, long long ldc, int* err,
-                           cudaStream_t st);
-bool tc_gemm_supported(long long M, int Nr, int Kr, long long lda, long long ldb, long long ldc);
+// Output layout: element (batch b, row m, column n) of C (complex64) lives at
+//   C + boff(b) + sum_g (m_g * sCm[g]) + sum_g (n_g * sCn[g])
+// where m = m_0 + mdim[0] * (m_1 + mdim[1] * ...), likewise n and b, and boff adds
+// coff[b_{coff_grp}] when coff is set.  Strides in complex elements.
+struct TcEpilogue {
+  float2* C;
+  long long M;          // rows of one batch entry
+  int N;                // complex columns
+  int nm, nn, nb;
+  int mdim[4], ndim[4], bdim[2];
+  long long sCm[4], sCn[4], sCb[2];
+  const long long* coff;
+  int coff_grp;
+};
 
-cudaError_t tf32_lo(const float* x, float* lo, long long n, cudaStream_t st);
+struct TcArgs {
+  TcEpilogue e;
+  long long nbatch;     // batch entries
+  int merged;           // 1: A rows run over nbatch * M (B shared by every entry)
+  int a_batched;        // A holds one M-row block per batch entry (else one, shared)
+  int b_batched;        // B holds one 2N-row block per batch entry (else one, shared)
+  int Kr;               // real K extent (2K); columns beyond the operands' widths read as 0
+  int tiles_m, tiles_n; // filled by tc_gemm_tf32x3
+  int* err;             // device flag set to 1 when a pipeline wait timed out
+};
 
-// Expand a complex operand E (complex64, element (n, k) at n1*sN1 + n2*sN2 + k1*sK1 +
-// k2*sK2 with n = n1*N2 + n2, k = k1*K2 + k2) into the real 2N x 2K block matrix.
-cudaError_t expand_b(const void* E, int N1, int N2, long long sN1, long long sN2, int K1, int K2, long long sK1,
-                     long long sK2, float* Bhi, float* Blo, cudaStream_t st);
+// A: [rowsA][Kr] FP32 (interleaved complex) with row pitch lda floats (its TF32
+// remainder is formed in shared memory); Bhi/Blo: [rowsB][Kr] expanded operand and
+// its TF32 remainder, pitch ldb.  Pitches must be multiples of 4 floats and
+// pointers 16-byte aligned.
+struct TcOperands {
+  const float *A, *Bhi, *Blo;
+  long long lda, ldb;
+};
+
+// x rounded to the nearest TF32 value (ties to even): 13 low mantissa bits cleared.
+__host__ __device__ inline float tf32_rn(float x) {
+#ifdef __CUDA_ARCH__
+  uint32_t u = __float_as_uint(x);
+#else
+  uint32_t u;
+  memcpy(&u, &x, 4);
+#endif
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  u &= 0xFFFFE000u;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+#endif
+}
+
+bool tc_available();
+// cudaErrorNotSupported when the shape or alignment does not fit the kernel.
+cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st);
+// Per-device error flag shared by every tensor-core launch (lazily allocated).
+int* tc_error_flag();
 
 }  // namespace tns

@@ -3,6 +3,7 @@
 #include "../../include/tns_testing.h"
 #include "linalg.cuh"
 #include "tc_gemm.cuh"
+#include "contract.cuh"
 #include "state.h"
 
 #include <vector>
@@ -60,6 +61,36 @@ extern "C" tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A, d
   return TNS_OK;
 }
 
+extern "C" tns_status tns_test_eigh32(int32_t batch, int32_t n, const float* A, double* lam, double* V,
+                                      void* stream) {
+  if (batch < 0 || n < 1 || n > 512 || !A || !lam || !V) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cf* work = nullptr;
+  int* status = nullptr;
+  int* sweeps = nullptr;
+  TNS_TRY_CUDA(cudaMalloc(&status, sizeof(int) * (batch > 0 ? batch : 1)));
+  TNS_TRY_CUDA(cudaMalloc(&sweeps, sizeof(int) * (batch > 0 ? batch : 1)));
+  if (!jacobi_fits_smem_f32(n)) {
+    long long np = n + (n & 1);
+    TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cf) * batch * 2 * np * np));
+  }
+  cudaError_t e = eigh_batched_f32((const cf*)A, (long long)n * n, n, n, batch, lam, (cd*)V, (long long)n * n, work,
+                                   status, st, sweeps);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  std::vector<int> hs(batch > 0 ? batch : 1), hw(batch > 0 ? batch : 1);
+  if (e == cudaSuccess && batch > 0) {
+    cudaMemcpy(hs.data(), status, sizeof(int) * batch, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hw.data(), sweeps, sizeof(int) * batch, cudaMemcpyDeviceToHost);
+    g_last_sweeps.assign(batch, 0);
+    for (int b = 0; b < batch; ++b) g_last_sweeps[b] = hs[b] == 0 ? hw[b] : -hw[b];
+  }
+  cudaFree(work);
+  cudaFree(status);
+  cudaFree(sweeps);
+  TNS_TRY_CUDA(e);
+  return TNS_OK;
+}
+
 extern "C" tns_status tns_test_eigh_sweeps(int32_t batch, int32_t* out) {
   if (!out || batch < 0 || (size_t)batch > g_last_sweeps.size()) { set_error("invalid argument"); return TNS_ERR_ARG; }
   for (int b = 0; b < batch; ++b) out[b] = g_last_sweeps[b];
@@ -102,26 +133,62 @@ extern "C" tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const flo
                                       void* stream) {
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C) { set_error("invalid argument"); return TNS_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  const int Kr = 2 * K, Nr = 2 * N;
-  if (!tc_gemm_supported(M, Nr, Kr, Kr, Kr, Nr)) { set_error("shape not supported by the tensor-core path"); return TNS_ERR_STATE; }
-  float *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;
-  int* err = nullptr;
-  TNS_TRY_CUDA(cudaMalloc(&Alo, sizeof(float) * M * Kr));
-  TNS_TRY_CUDA(cudaMalloc(&Bhi, sizeof(float) * (size_t)Nr * Kr));
-  TNS_TRY_CUDA(cudaMalloc(&Blo, sizeof(float) * (size_t)Nr * Kr));
-  TNS_TRY_CUDA(cudaMalloc(&err, sizeof(int)));
-  cudaMemsetAsync(err, 0, sizeof(int), st);
-  cudaError_t e = tf32_lo(A, Alo, M * Kr, st);
-  if (e == cudaSuccess) e = expand_b(B, N, 1, K, 0, K, 1, 1, 0, Bhi, Blo, st);
-  if (e == cudaSuccess) e = tc_gemm_tf32x3(A, Alo, M, Kr, Kr, Bhi, Blo, Nr, Kr, C, Nr, err, st);
-  int herr = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(Alo);
-  cudaFree(Bhi);
-  cudaFree(Blo);
-  cudaFree(err);
+  ContractTiming tm;
+  tm.force_tc = true;
+  cudaError_t e = contract(view((void*)A, "mk", {M, K}), view((void*)B, "nk", {N, K}), view(C, "mn", {M, N}),
+                           Prec::TF32X3, st, make_double2(1.0, 0.0), make_double2(0.0, 0.0), nullptr, &tm);
+  if (e == cudaErrorNotSupported) { set_error("shape not supported by the tensor-core path"); return TNS_ERR_STATE; }
   TNS_TRY_CUDA(e);
+  TNS_TRY_CUDA(cudaStreamSynchronize(st));
+  int* f = tc_error_flag();
+  int herr = 0;
+  if (f) {
+    TNS_TRY_CUDA(cudaMemcpy(&herr, f, sizeof(int), cudaMemcpyDeviceToHost));
+    TNS_TRY_CUDA(cudaMemset(f, 0, sizeof(int)));
+  }
   if (herr) { set_error("tensor-core GEMM pipeline wait timed out"); return TNS_ERR_NUMERIC; }
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_test_contract(const char* labels_a, const int64_t* dims_a, const int64_t* strides_a,
+                                        int32_t conj_a, const void* A, const char* labels_b, const int64_t* dims_b,
+                                        const int64_t* strides_b, int32_t conj_b, const void* B, const char* labels_c,
+                                        const int64_t* dims_c, const int64_t* strides_c, void* C, int32_t mode,
+                                        void* stream) {
+  if (!labels_a || !labels_b || !labels_c || !A || !B || !C || mode < 0 || mode > 2) {
+    set_error("invalid argument");
+    return TNS_ERR_ARG;
+  }
+  auto mk = [](const char* lab, const int64_t* d, const int64_t* st, int cj, const void* p) {
+    TView v;
+    v.ptr = const_cast<void*>(p);
+    v.labels = lab;
+    for (size_t i = 0; i < v.labels.size(); ++i) {
+      v.dim.push_back(d[i]);
+      v.stride.push_back(st[i]);
+    }
+    v.conj = cj != 0;
+    return v;
+  };
+  cudaStream_t st = (cudaStream_t)stream;
+  ContractTiming tm;
+  tm.force_tc = (mode == 1);
+  const Prec pr = mode == 0 ? Prec::F32 : (mode == 1 ? Prec::TF32X3 : Prec::F64);
+  cudaError_t e = contract(mk(labels_a, dims_a, strides_a, conj_a, A), mk(labels_b, dims_b, strides_b, conj_b, B),
+                           mk(labels_c, dims_c, strides_c, 0, C), pr, st, make_double2(1.0, 0.0),
+                           make_double2(0.0, 0.0), nullptr, &tm);
+  if (e == cudaErrorNotSupported) { set_error("contraction not supported by the tensor-core path"); return TNS_ERR_STATE; }
+  if (e == cudaErrorInvalidValue) { set_error("inconsistent contraction views"); return TNS_ERR_ARG; }
+  TNS_TRY_CUDA(e);
+  TNS_TRY_CUDA(cudaStreamSynchronize(st));
+  if (mode == 1) {
+    int* f = tc_error_flag();
+    int herr = 0;
+    if (f) {
+      TNS_TRY_CUDA(cudaMemcpy(&herr, f, sizeof(int), cudaMemcpyDeviceToHost));
+      TNS_TRY_CUDA(cudaMemset(f, 0, sizeof(int)));
+    }
+    if (herr) { set_error("tensor-core GEMM pipeline wait timed out"); return TNS_ERR_NUMERIC; }
+  }
   return TNS_OK;
 }
