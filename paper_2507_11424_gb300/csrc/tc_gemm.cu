@@ -8,19 +8,20 @@
 //   [ Bi   Br ]   rows 2n+1 (imaginary part)
 // interleaved by k, so C comes out interleaved.  Precision: kind::tf32 with a
 // three-pass split product A_hi B_hi + A_hi B_lo + A_lo B_hi, where hi is the
-// value rounded to the nearest TF32 (10 explicit mantissa bits) and lo the
-// remainder rounded the same way (|lo| <= 2^-11 |x|); each real product is then
+// value rounded to the nearest TF32 (10 explicit mantissa bits; ties to even for
+// B, away from zero for A) and lo the remainder rounded the same way
+// (|lo| <= 2^-11 |x|); each real product is then
 // within 3 * 2^-22 |a||b| (the dropped lo*lo term and the two lo roundings), and
 // all products accumulate in one FP32 TMEM tile.
 //
-// Kernel: one 128 x BN output tile per CTA (BN = 128 or 256 real columns), 128
+// Kernel: one 128 x BN output tile per CTA (BN = 128 or 256 real columns), 320
 // threads.  Thread 0 issues TMA loads (128B-swizzled, 32 FP32 of K per row) of
-// A, B_hi and B_lo into a ring of 2 (BN = 256) or 3 (BN = 128) stages guarded by
-// mbarriers; warps 2-3 derive A_lo from the staged A tile in shared memory (no
-// HBM pass over A); thread 32 issues the three tcgen05.mma products per k-step
+// A (own mbarrier), B_hi and B_lo into a ring of 2 (BN = 256) or 3 (BN = 128)
+// stages; warps 2-9 split the staged A tile in shared memory into its TF32 hi and
+// lo parts (no HBM pass over A); thread 32 issues the three tcgen05.mma products per k-step
 // (M=128, N=BN, K=8 per instruction) and releases each stage with
-// tcgen05.commit; all four warps then read the accumulator from TMEM (each warp
-// its 32 lanes) and store it through the output's index decomposition (runs of
+// tcgen05.commit; warps 0-3 then read the accumulator from TMEM (each warp its 32
+// lanes) and store it through the output's index decomposition (runs of
 // 16 contiguous complex outputs as 16-byte vector stores).  Every wait has a 1 s
 // time limit after which the kernel raises an error flag and exits.
 #include <cuda.h>
@@ -39,6 +40,10 @@ constexpr int BM = 128, BKF = 32;
 constexpr size_t TILE_A = (size_t)BM * BKF * sizeof(float);   // 16 KB
 // pipeline depth: each stage holds A, A_lo, B_hi, B_lo (96 KB at BN = 256, 64 KB at BN = 128)
 template <int BN> struct Stages { static constexpr int value = BN == 256 ? 2 : 3; };
+// warps: 0 = TMA producer (thread 0), 1 = MMA issuer (thread 32), 2..2+CONV_WARPS-1 =
+// converters; warps 0-3 also run the epilogue (TMEM lane quarter = warp index)
+constexpr int CONV_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * CONV_WARPS;
 template <int BN> constexpr size_t smem_bytes() {
   return Stages<BN>::value * (2 * TILE_A + 2 * (size_t)BN * BKF * sizeof(float)) + 1024 + 256;
 }
@@ -80,6 +85,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
       : "memory");
+}
+// round to nearest TF32, ties away from zero (hardware conversion)
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -149,7 +160,7 @@ __device__ __forceinline__ long long tc_batch_off(const TcEpilogue& e, long long
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBhi,
                       const __grid_constant__ CUtensorMap mBlo, const TcArgs p) {
   constexpr int STAGES = Stages<BN>::value;
@@ -162,8 +173,9 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   float* sAlo = sA + STAGES * BM * BKF;            // [STAGES][BM*BKF]
   float* sB = sAlo + STAGES * BM * BKF;            // [STAGES][BN*BKF]
   float* sBlo = sB + STAGES * BN * BKF;            // [STAGES][BN*BKF]
-  uint64_t* full = reinterpret_cast<uint64_t*>(sBlo + STAGES * BN * BKF);
-  uint64_t* lo_ready = full + STAGES;
+  uint64_t* full_a = reinterpret_cast<uint64_t*>(sBlo + STAGES * BN * BKF);   // A tile landed
+  uint64_t* full = full_a + STAGES;                                               // B tiles landed
+  uint64_t* lo_ready = full + STAGES;                                             // A split done
   uint64_t* empty = lo_ready + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -196,8 +208,9 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_a[s], 1);
       mbar_init(&full[s], 1);
-      mbar_init(&lo_ready[s], 64);
+      mbar_init(&lo_ready[s], 32 * CONV_WARPS);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
@@ -223,8 +236,10 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
       if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, deadline)) { *abort_flag = 1; break; }
-      mbar_expect_tx(&full[s], (uint32_t)(TILE_A + 2 * TILE_B));
-      tma_load_2d(sA + s * BM * BKF, &mA, &full[s], it * BKF, a_row0);
+      // A first, on its own barrier, so the converters start while B is in flight
+      mbar_expect_tx(&full_a[s], (uint32_t)TILE_A);
+      tma_load_2d(sA + s * BM * BKF, &mA, &full_a[s], it * BKF, a_row0);
+      mbar_expect_tx(&full[s], (uint32_t)(2 * TILE_B));
       tma_load_2d(sB + s * BN * BKF, &mBhi, &full[s], it * BKF, b_row0);
       tma_load_2d(sBlo + s * BN * BKF, &mBlo, &full[s], it * BKF, b_row0);
       issued = it + 1;
@@ -232,8 +247,10 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
     if (*abort_flag) {
       // let copies already in flight land before the CTA exits (bounded)
       const unsigned long long d2 = gtimer() + WAIT_NS / 10;
-      for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+      for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it) {
+        mbar_wait(&full_a[it % STAGES], (it / STAGES) & 1, d2);
         mbar_wait(&full[it % STAGES], (it / STAGES) & 1, d2);
+      }
     }
   } else if (threadIdx.x == 32) {
     // MMA issuer: A B_hi + A B_lo + A_lo B_hi per k-block
@@ -263,21 +280,22 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
     mma_commit(done);
     if (!ok) *abort_flag = 1;
   } else if (warp >= 2) {
-    // converters: split the staged A tile in place into hi = tf32_rn(A) and
-    // lo = tf32_rn(A - hi), elementwise, so the swizzled layout carries over unchanged
+    // converters: split the staged A tile in place into hi = tf32(A) and
+    // lo = tf32(A - hi) (round to nearest), elementwise, so the swizzled layout carries
+    // over unchanged
     const int t = threadIdx.x - 64;
     for (int it = 0; it < nkb; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (it / STAGES) & 1;
-      if (*abort_flag || !mbar_wait(&full[s], ph, deadline)) { *abort_flag = 1; break; }
+      if (*abort_flag || !mbar_wait(&full_a[s], ph, deadline)) { *abort_flag = 1; break; }
       float4* hi = reinterpret_cast<float4*>(sA + s * BM * BKF);
       float4* dst = reinterpret_cast<float4*>(sAlo + s * BM * BKF);
 #pragma unroll 4
-      for (int i = t; i < BM * BKF / 4; i += 64) {
+      for (int i = t; i < BM * BKF / 4; i += 32 * CONV_WARPS) {
         const float4 v = hi[i];
-        const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
         hi[i] = h;
-        dst[i] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+        dst[i] = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
       }
       fence_proxy_async();
       mbar_arrive(&lo_ready[s]);
@@ -286,7 +304,7 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
   __syncwarp();
   const bool ready = mbar_wait(done, 0, deadline) && !*abort_flag;
   tc_fence_after();
-  if (ready) {
+  if (ready && warp < 4) {
     const long long r = m0 + warp * 32 + lane;
     long long b = bz, m = r;
     bool valid;
@@ -323,7 +341,7 @@ tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_const
         }
       }
     }
-  } else if (threadIdx.x == 0 && p.err) {
+  } else if (!ready && threadIdx.x == 0 && p.err) {
     atomicExch(p.err, 1);
   }
   tc_fence_before();
@@ -390,7 +408,7 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
   a.tiles_m = (int)tm;
   const long long tiles = tm * a.tiles_n * (a.merged ? 1 : a.nbatch);
   if (tiles >= (1LL << 31)) return cudaErrorNotSupported;
-  tc_gemm_tf32x3_kernel<BN><<<(unsigned)tiles, 128, SMEM, st>>>(ma, mbhi, mblo, a);
+  tc_gemm_tf32x3_kernel<BN><<<(unsigned)tiles, TC_THREADS, SMEM, st>>>(ma, mbhi, mblo, a);
   return cudaGetLastError();
 }
 
