@@ -68,10 +68,12 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
   extern __shared__ double4 smraw4[];
   __shared__ T cs_c[256], cs_s[256], cs_d[256];
   __shared__ C cs_e[256];
+  __shared__ int cs_p[256], cs_q[256];
   __shared__ T red[JAC_THREADS / 32];
   __shared__ T floor_s;
   __shared__ int nrot;
   const int b = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   const int np = n + (n & 1), half = np / 2;
   C* a = use_smem ? reinterpret_cast<C*>(smraw4) : work + (long long)b * 2 * np * np;
   C* v = a + (long long)np * np;
@@ -104,6 +106,8 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
       for (int i = tid; i < half; i += blockDim.x) {
         int p, q;
         rr_pair(r, i, np, p, q);
+        cs_p[i] = p;
+        cs_q[i] = q;
         T app = a[p * np + p].x, aqq = a[q * np + q].x;
         C apq = a[p * np + q];
         T ab = sqrt(cabs2(apq));
@@ -119,38 +123,40 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
         cs_c[i] = c; cs_s[i] = s; cs_e[i] = e; cs_d[i] = dl;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * np; idx += blockDim.x) {       // rows: J^H A
-        int i = idx / np, j = idx % np, p, q;
+      // one warp per rotation, lanes along the row / column (no index division)
+      for (int i = warp; i < half; i += nwarp) {                       // rows: J^H A
         if (cs_s[i] == 0) continue;
-        rr_pair(r, i, np, p, q);
-        T c = cs_c[i], s = cs_s[i];
-        C e = cs_e[i];
-        C ap = a[p * np + j], aq = a[q * np + j];
-        C eaq = cmul(e, aq);
-        a[p * np + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-        a[q * np + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+        const int p = cs_p[i], q = cs_q[i];
+        const T c = cs_c[i], s = cs_s[i];
+        const C e = cs_e[i];
+        for (int j = lane; j < np; j += 32) {
+          C ap = a[p * np + j], aq = a[q * np + j];
+          C eaq = cmul(e, aq);
+          a[p * np + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+          a[q * np + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+        }
       }
       __syncthreads();
-      for (int idx = tid; idx < half * np; idx += blockDim.x) {       // columns: (J^H A) J and V J
-        int i = idx / np, j = idx % np, p, q;
+      for (int i = warp; i < half; i += nwarp) {                       // columns: (J^H A) J and V J
         if (cs_s[i] == 0) continue;
-        rr_pair(r, i, np, p, q);
-        T c = cs_c[i], s = cs_s[i];
-        C ec = cconj(cs_e[i]);
-        C ap = a[j * np + p], aq = a[j * np + q];
-        C eaq = cmul(ec, aq);
-        a[j * np + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-        a[j * np + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
-        C vp = v[j * np + p], vq = v[j * np + q];
-        C evq = cmul(ec, vq);
-        v[j * np + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
-        v[j * np + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
+        const int p = cs_p[i], q = cs_q[i];
+        const T c = cs_c[i], s = cs_s[i];
+        const C ec = cconj(cs_e[i]);
+        for (int j = lane; j < np; j += 32) {
+          C ap = a[j * np + p], aq = a[j * np + q];
+          C eaq = cmul(ec, aq);
+          a[j * np + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+          a[j * np + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+          C vp = v[j * np + p], vq = v[j * np + q];
+          C evq = cmul(ec, vq);
+          v[j * np + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
+          v[j * np + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
+        }
       }
       __syncthreads();
       for (int i = tid; i < half; i += blockDim.x) {                   // exact 2x2 result
         if (cs_s[i] == 0) continue;
-        int p, q;
-        rr_pair(r, i, np, p, q);
+        const int p = cs_p[i], q = cs_q[i];
         a[p * np + q] = mk((T)0, (T)0);
         a[q * np + p] = mk((T)0, (T)0);
       }

@@ -261,6 +261,73 @@ __global__ void transpose_conj_kernel(const C* __restrict__ T, C* __restrict__ T
   }
 }
 
+// Gram matrices of tall complex64 panels: G[b] = Y[b]^H Y[b] with Y [b][M][n]
+// (row-major), G [b][n][n], FP32 accumulation on the CUDA cores.  Block (split,
+// b) sums rows [split * rows_per, ...) of entry b into P[b][split]; thread (x, y)
+// of the (nb x nb) block, nb = ceil(n / 4), owns the 4 x 4 tile G[4y.., 4x..]; Y
+// streams through shared memory 32 rows at a time.  gram_reduce_kernel adds the
+// splits in index order (deterministic).
+constexpr int GRAM_MAX_N = 128;
+__global__ void gram_partial_kernel(const cf* __restrict__ Y, long long M, int n, long long rows_per,
+                                    cf* __restrict__ P) {
+  __shared__ cf ys[32][GRAM_MAX_N];
+  const long long b = blockIdx.y;
+  const int split = blockIdx.x;
+  const long long r0 = split * rows_per, r1 = min(M, r0 + rows_per);
+  const cf* src = Y + b * M * n;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (long long m0 = r0; m0 < r1; m0 += 32) {
+    const int rows = (int)(r1 - m0 < 32 ? r1 - m0 : 32);
+    for (int r = ty; r < 32; r += blockDim.y)
+      for (int c = tx; c < n; c += blockDim.x) ys[r][c] = r < rows ? src[(m0 + r) * n + c] : make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int r = 0; r < rows; ++r) {
+      float2 a[4], v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int ci = 4 * ty + i, cj = 4 * tx + i;
+        a[i] = ci < n ? ys[r][ci] : make_float2(0.f, 0.f);
+        v[i] = cj < n ? ys[r][cj] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {          // acc += conj(a_i) v_j
+          acc[i][j].x = fmaf(a[i].x, v[j].x, fmaf(a[i].y, v[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, v[j].y, fmaf(-a[i].y, v[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  cf* dst = P + (b * gridDim.x + split) * (long long)n * n;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ci = 4 * ty + i, cj = 4 * tx + j;
+      if (ci < n && cj < n) dst[(long long)ci * n + cj] = acc[i][j];
+    }
+}
+
+__global__ void gram_reduce_kernel(const cf* __restrict__ P, int splits, long long nn, long long total,
+                                   cf* __restrict__ G) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / nn, e = i % nn;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = 0; k < splits; ++k) {
+      const float2 v = P[(b * splits + k) * nn + e];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    G[i] = acc;
+  }
+}
+
 static cudaError_t pcontract(tns_state* s, int cls, const TView& A, const TView& B, const TView& C, Prec p) {
   cudaEvent_t ev = s->prof.begin(s->st);
   double fl = 0.0;
@@ -284,6 +351,38 @@ static cudaError_t pcontract(tns_state* s, int cls, const TView& A, const TView&
     if (p == Prec::TF32X3 && cls == PC_SWEEP) c = PC_SWEEP_SIMT;
     s->prof.end(c, ev, fl, s->st);
   }
+  return e;
+}
+
+// G = Y^H Y per batch entry (Y: S x M x n): the dedicated Gram kernels for complex64
+// panels with n <= 128, else the general contraction.
+static cudaError_t pgram(tns_state* s, Prec p, const void* Y, long long S, long long M, int n, void* G) {
+  if (p == Prec::F64 || n > GRAM_MAX_N || S > 65535)
+    return pcontract(s, PC_ZIP, view(const_cast<void*>(Y), "Smc", {S, M, n}, true),
+                     view(const_cast<void*>(Y), "Sme", {S, M, n}), view(G, "Sce", {S, n, n}), p);
+  // enough blocks for several per SM, each with at least 128 rows
+  int splits = (int)std::max<long long>(1, std::min<long long>((M + 127) / 128, (4 * 152 + S - 1) / S));
+  const long long rows_per = (M + splits - 1) / splits;
+  splits = (int)((M + rows_per - 1) / rows_per);
+  cudaEvent_t ev = s->prof.begin(s->st);
+  cf* P = (cf*)G;
+  if (splits > 1) {
+    cudaError_t e = cudaMallocAsync((void**)&P, sizeof(cf) * (size_t)S * splits * n * n, s->st);
+    if (e != cudaSuccess) return e;
+  }
+  const int nb = (n + 3) / 4;
+  gram_partial_kernel<<<dim3((unsigned)splits, (unsigned)S), dim3(nb, nb), 0, s->st>>>((const cf*)Y, M, n, rows_per, P);
+  s->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (splits > 1) {
+    const long long total = S * (long long)n * n;
+    if (e == cudaSuccess)
+      gram_reduce_kernel<<<nblk(total), 256, 0, s->st>>>(P, splits, (long long)n * n, total, (cf*)G);
+    s->launches++;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFreeAsync(P, s->st);
+  }
+  s->prof.end(PC_ZIP_SIMT, ev, 8.0 * (double)S * M * n * n, s->st);
   return e;
 }
 
@@ -417,8 +516,7 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
   cd* work = nullptr;
   if (!chol_fits_smem(kk)) TNS_TRY(wsget(s, "z_cwork", sizeof(cd) * S * 2 * kk * kk, (void**)&work));
   auto pass = [&](void* src, void* dst, double shift) -> tns_status {
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(src, "Smc", {S, M, kk}, true), view(src, "Sme", {S, M, kk}),
-                           view(G, "Sce", {S, kk, kk}), cx.gp));
+    TNS_TRY_CUDA(pgram(s, cx.gp, src, S, M, kk, G));
     cudaEvent_t ev = s->prof.begin(cx.st);
     TNS_TRY_CUDA(chol_w_batched(G, cx.f64, kk, (int)S, shift, Wm, cx.f64, work, cx.st));
     s->prof.end(PC_EIGH, ev, 0.0, cx.st);
@@ -507,8 +605,7 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   } else {
     void* H32;
     TNS_TRY(wsget(s, "z_H32", sizeof(cf) * S * kk * kk, &H32));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sne", {S, N, kk}, true), view(B, "Snf", {S, N, kk}),
-                           view(H32, "Sef", {S, kk, kk}), cx.gp));
+    TNS_TRY_CUDA(pgram(s, cx.gp, B, S, N, kk, H32));
     cf* work = nullptr;
     if (!jacobi_fits_smem_f32(kk)) TNS_TRY(wsget(s, "z_jwork32", sizeof(cf) * S * 2 * np * np, (void**)&work));
     cudaEvent_t ev = s->prof.begin(s->st);
