@@ -31,12 +31,14 @@ def state(tmp_path_factory):
     return st, fixture.load(path), cfg, bits
 
 
-# Tolerances.  FP64: rounding only (1e-8).  Mixed (FP32 contractions): at chi_b = 64
-# this state is truncated hard, and replaying the same bitstrings in FP64 with a
-# different range-finder test matrix already moves single conditionals by ~2.6e-2;
-# FP32 rounding moves them by ~2e-3 at most.  The mixed bar is 5e-3 on the largest
-# conditional and 5e-4 on the mean over all conditionals of the sample.
-@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT, 5e-3), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
+# Tolerances.  FP64: rounding only (1e-8).  Mixed (complex64 storage, TF32x3 tensor-core
+# contractions, FP32 Gram / Cholesky / Jacobi in the truncation): at chi_b = 64 this
+# state is truncated hard, and replaying the same bitstrings in FP64 with a different
+# range-finder test matrix already moves single conditionals by ~2.6e-2 -- the
+# method's own spread between equally valid runs.  FP32-level rounding moves them by
+# up to ~6e-3.  The mixed bar is 1e-2 on the largest conditional (below that spread)
+# and 1e-3 on the mean over all conditionals of the sample.
+@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT, 1e-2), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
 def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
     st, t, cfg, bits = state
     R = cfg["chi_b"]
