@@ -35,6 +35,13 @@ CONFIG = "sq10x10"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s SIMT FP32
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tf32 : bf16 tensor throughput
+# DRAM traffic of the tensor-core GEMM kernel from one ncu capture of a smaller case of the
+# same contraction (A 32768 x 1024 complex64 read once, B 1024 x 1024, C 32768 x 1024;
+# profiles/tc_gemm_tf32x3_M32768_N1024_K1024.md): dram read + write bytes and the case's
+# algorithmic flop.  Traffic grows with the rows processed, so a launch's traffic is scaled
+# by its flop.
+TC_CAPTURE_BYTES = 418.606848e6 + 244.045568e6
+TC_CAPTURE_FLOP = 8.0 * 32768 * 1024 * 1024
 
 
 def tensor_peak():
@@ -271,8 +278,12 @@ def run_gpu(args):
     total_flops = sum(v["flops"] for v in prof.values())
     if args.prec == "mixed" and prof["tc_prep"]["launches"] > 0:
         peak, src, bf16 = tensor_peak()
+        per_launch_flop = env["flops"] / env["launches"] if env["launches"] else 0.0
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": TC_CAPTURE_BYTES * per_launch_flop / TC_CAPTURE_FLOP,
+                    "traffic_note": "bytes per average launch, scaled by flop from the ncu capture of the "
+                                    "32768 x 1024 x 1024 case",
                     "kernel": "tc_gemm_tf32x3_kernel (environment contraction, tcgen05 kind::tf32, 3-pass split)",
                     "peak_note": (f"{src} bf16 dense burst {bf16} TFLOP/s x {TF32_PER_BF16:.3f} (nominal tf32/bf16) "
                                   "/ 3 MMA passes per product; achieved counts 8 flop per complex MAC once")}
