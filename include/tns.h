@@ -43,8 +43,10 @@ typedef enum {
 
 typedef enum {
   TNS_PREC_FP64 = 0,  /* every contraction and factorisation in FP64 */
-  TNS_PREC_MIXED = 1  /* sampler contractions in FP32 complex; Gram matrices, small
-                         eigenproblems (the truncation), probabilities and log q in FP64 */
+  TNS_PREC_MIXED = 1  /* complex64 storage; contractions on the tensor cores as a TF32
+                         three-pass split (FP32-level accuracy) or on FP32 CUDA cores;
+                         truncation Grams, Cholesky and Jacobi in FP32; probabilities and
+                         log q in FP64 */
 } tns_prec;
 
 typedef struct tns_state tns_state; /* opaque, library-owned */
