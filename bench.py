@@ -69,6 +69,27 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(rank: int) -> int:
+    """Sampling seed of a replica: distinct per rank, so the ranks draw independent samples."""
+    return 1000003 * (rank + 1)
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's value (the job's time); identity on one rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, batch: int, steps: int, seconds: float) -> float:
+    """Whole-job samples/s: every rank draws `batch` samples per step."""
+    return world * batch * steps / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,7 +246,7 @@ def run_gpu(args):
     n_sites = lat.n_qubits
     bits_d = torch.zeros((B, n_sites), dtype=torch.uint8, device="cuda")
     logq_d = torch.zeros(B, dtype=torch.float64, device="cuda")
-    seed0 = 1000003 * (rank + 1)
+    seed0 = rank_seed(rank)
     for i in range(args.warmup):
         st.sample(R, B, seed0 + i, out=(bits_d, logq_d, None))
     torch.cuda.synchronize()
@@ -250,11 +271,8 @@ def run_gpu(args):
     prof = st.profile_read()
     st.profile(False)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = job_rate(world, B, args.steps, ms / 1e3)
     # end to end through the public API: host-visible results every step
     bits_h = torch.empty((B, n_sites), dtype=torch.uint8, pin_memory=True)
     logq_h = torch.empty(B, dtype=torch.float64, pin_memory=True)
@@ -268,10 +286,7 @@ def run_gpu(args):
         logq_h.copy_(logq_d, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.time() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     sector = float((bits_h.numpy().sum(axis=1) == int(bits.sum())).mean())
     env = prof["env_gemm"]
     achieved = env["flops"] / (env["ms"] / 1e3) / 1e12 if env["ms"] > 0 else None
@@ -301,7 +316,7 @@ def run_gpu(args):
         "config": {"workload": "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64",
                    "samples_per_step": B, "precision_path": args.prec, "l2": "working set > L2, no flush",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": world * B * args.steps / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": job_rate(world, B, args.steps, e2e_s), "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": B * n_sites + 8 * B},
         "roofline": roofline,
         "cpu_baseline": cpu_res,
