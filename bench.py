@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "samples/s at <=1e-3 marginal error vs plain sampler; boundary-MPS TFLOP/s"
 CONFIG = "sq10x10"
+WORKLOAD = "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s SIMT FP32
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tf32 : bf16 tensor throughput
@@ -313,8 +314,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64" if args.prec == "mixed" else "c128", "data": "synthetic",
-        "config": {"workload": "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64",
-                   "samples_per_step": B, "precision_path": args.prec, "l2": "working set > L2, no flush",
+        "config": {"workload": WORKLOAD, "samples_per_step": B, "precision_path": args.prec, "l2": "working set > L2, no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": job_rate(world, B, args.steps, e2e_s), "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": B * n_sites + 8 * B},
@@ -381,8 +381,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64",
-                      "step": "one row of one sample"},
+           "config": {"workload": WORKLOAD, "samples_per_step": args.batch, "parallelism": f"replicas x{world}",
+                      "step": "one row of one sample (the oracle's rate is scaled to samples/s)"},
            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": f"one row of one sample per step ({args.steps} timed steps), scaled by 1/{H}"},
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
