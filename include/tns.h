@@ -151,11 +151,11 @@ tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* log_norm);
 /* Select the precision of later tns_sample / tns_amplitude calls. */
 tns_status tns_set_precision(tns_state* s, tns_prec prec);
 
-/* Select how the mixed-precision path runs its environment contractions (the
- * dominant GEMMs of the marginal sweeps): 1 (default) = tcgen05 tensor cores,
- * kind::tf32 with a three-pass hi/lo split product (FP32-level accuracy);
- * 0 = FP32 CUDA cores.  Shapes the tensor-core kernel does not support fall back
- * to CUDA cores automatically. */
+/* Select how the mixed-precision path runs its contractions: 1 (default) =
+ * every contraction of at least 2^24 complex multiply-adds on the tcgen05 tensor
+ * cores, kind::tf32 with a three-pass hi/lo split product (FP32-level accuracy),
+ * smaller ones on FP32 CUDA cores; 0 = all on FP32 CUDA cores.  Shapes the
+ * tensor-core kernel does not support fall back to CUDA cores automatically. */
 tns_status tns_set_tensor_cores(tns_state* s, int32_t enable);
 
 /* Query: grid rows/cols after orientation, whether it was transposed, and the
