@@ -324,3 +324,68 @@ def amplitude(tns, R, bits, seed, gram_cut=ORTH_SHIFT, exact=False):
     if abs(z) == 0:
         return -np.inf, 0.0
     return log_abs + float(np.log(abs(z))), float(np.angle(z))
+
+
+# ------------------------------------------------------- direct marginals
+class _Flipped:
+    """The same TNS read upside down: row b -> H-1-b, up and down legs exchanged."""
+
+    def __init__(self, tns):
+        self.H, self.W = tns.H, tns.W
+        self.T = [[np.transpose(tns.T[tns.H - 1 - b][c], (0, 3, 2, 1, 4)) for c in range(tns.W)]
+                  for b in range(tns.H)]
+
+
+def direct_marginals(tns, R, gram_cut=ORTH_SHIFT, exact=False):
+    """Sample-free marginals <n_q> = <psi|P1_q|psi>/<psi|psi> for every qubit and
+    <n_q n_q'> for every pair in the same grid row (NaN for pairs in different
+    rows), by boundary-MPS contraction of the norm network <psi|psi>.
+
+    Row b is contracted exactly between its top environment (rows 0..b-1, the
+    bottom environments of the upside-down TNS) and its bottom environment E[b+1]
+    (rows b+1..H-1), both compressed to rank R as in norm_envs.  Exact when R
+    covers the environments' ranks.  Returns (one [n], two [n, n]).
+    """
+    H, W = tns.H, tns.W
+    E, _ = norm_envs(tns, R, gram_cut=gram_cut, exact=exact)
+    Ef, _ = norm_envs(_Flipped(tns), R, gram_cut=gram_cut, exact=exact)
+    n = int((tns.cell_qubit >= 0).sum())
+    one = np.full(n, np.nan)
+    two = np.full((n, n), np.nan)
+    P = [np.eye(2, dtype=np.complex128), np.diag([0.0, 1.0]).astype(np.complex128)]
+    for b in range(H):
+        U = Ef[H - b]                 # sites [e, d, dbar, e'] on row b's up legs (flipped: down legs)
+        D = E[b + 1]                  # sites [f, d, dbar, f'] on row b's down legs
+
+        def transfer(c, op):
+            t = tns.T[b][c]                                              # s, u, l, d, r
+            s = t.shape[0]
+            o = np.eye(s, dtype=np.complex128) if (op is None or s == 1) else op
+            # T[e l lb f, e' r rb f'] = U[e,u,ub,e'] t[s,u,l,d,r] o[s,s'] conj t[s',ub,lb,db,rb] D[f,d,db,f']
+            X = np.einsum("aubA,sulDr,st,tbmEq,fDEF->almfArqF", U[c], t, o, t.conj(), D[c], optimize=True)
+            sh = X.shape
+            return X.reshape(sh[0] * sh[1] * sh[2] * sh[3], sh[4] * sh[5] * sh[6] * sh[7])
+
+        I = [transfer(c, None) for c in range(W)]
+        left = [np.ones((1,), dtype=np.complex128)]
+        for c in range(W):
+            left.append(left[-1] @ I[c])
+        right = [np.ones((1,), dtype=np.complex128)] * (W + 1)
+        for c in range(W - 1, -1, -1):
+            right[c] = I[c] @ right[c + 1]
+        norm = left[W].reshape(()).item()
+        qs = [(c, int(tns.cell_qubit[b, c])) for c in range(W) if tns.cell_qubit[b, c] >= 0]
+        T1 = {c: transfer(c, P[1]) for c, _ in qs}
+        for c, q in qs:
+            one[q] = float(np.real((left[c] @ T1[c] @ right[c + 1]).item() / norm))
+            two[q, q] = one[q]
+        for i, (ci, qi) in enumerate(qs):
+            v = left[ci] @ T1[ci]
+            for cj, qj in qs[i + 1:]:
+                for c in range(ci + 1, cj):
+                    v = v @ I[c]
+                val = float(np.real((v @ T1[cj] @ right[cj + 1]).item() / norm))
+                two[qi, qj] = two[qj, qi] = val
+                v = v @ I[cj]
+                ci = cj
+    return one, two

@@ -1,0 +1,52 @@
+"""Pins of the oracle's direct (sample-free) marginals, oracle/bmps.direct_marginals:
+brute-force statevector marginals of the same TNS when the boundary rank covers the
+environments, including a transposed (ladder) grid with empty cells."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import bmps, metrics
+from oracle.tns import GridTNS
+
+
+def _state(lat, bits, groups, chi):
+    t = GridTNS(lat.grid_rc, lat.edges, bits)
+    for g in groups:
+        t.apply_group(g, chi)
+        t.bp(500, 1e-12)
+    return t
+
+
+@pytest.mark.parametrize("kind", ["su4_3x3", "heis_4x4_truncated", "ladder"])
+def test_direct_marginals_equal_bruteforce(kind):
+    if kind == "su4_3x3":
+        lat = w.square(3, 3)
+        bits = w.domain_wall_bits(lat)
+        t = _state(lat, bits, w.random_su4_circuit(lat, 1, seed=5), 16)
+    elif kind == "heis_4x4_truncated":
+        lat = w.square(4, 4)
+        bits = w.domain_wall_bits(lat)
+        t = _state(lat, bits, w.heisenberg_circuit(lat, 2, 0.2), 4)     # chi = 4 truncates
+    else:
+        lat = w.ladder(4)
+        groups, bits = w.lucj_like_circuit(lat, reps=1, seed=3)
+        t = _state(lat, bits, groups, 16)
+    one, two = bmps.direct_marginals(t, 256)
+    o_ref, t_ref = metrics.marginals_from_statevector(t.statevector_bruteforce())
+    assert np.abs(one - o_ref).max() < 1e-10
+    mask = ~np.isnan(two)
+    assert mask.sum() >= len(one)
+    assert np.abs(two[mask] - t_ref[mask]).max() < 1e-10
+    assert np.allclose(np.diag(two), one)
+
+
+def test_first_site_marginal_equals_first_sampler_conditional():
+    """The first qubit of the first row has no prefix: its sampler conditional q(0)
+    is 1 - <n> (two different contraction orders of the same network)."""
+    lat = w.square(3, 3)
+    bits = w.domain_wall_bits(lat)
+    t = _state(lat, bits, w.random_su4_circuit(lat, 1, seed=9), 16)
+    one, _ = bmps.direct_marginals(t, 64)
+    _, _, q0 = bmps.sample(t, 64, 1, seed=3)
+    q = int(t.cell_qubit[0, 0])
+    assert abs(q0[0, q] - (1.0 - one[q])) < 1e-10
