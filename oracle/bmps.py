@@ -152,6 +152,14 @@ def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT
     return out, log_scale
 
 
+def compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT, fit_sweeps=0):
+    """The zip-up compression, followed by ``fit_sweeps`` sweeps of one-site
+    variational fitting when fit_sweeps > 0 (the paper's compressor)."""
+    if fit_sweeps > 0:
+        return fit_compress(mps, mpo, R, seed, stage, row, sweeps=fit_sweeps, exact=exact, gram_cut=gram_cut)
+    return zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut)
+
+
 def mirror_mps(mps):
     """Reverse the site order of an MPS (swap each site's bond axes)."""
     return [np.swapaxes(x, 0, x.ndim - 1) for x in reversed(mps)]
@@ -174,7 +182,7 @@ def row_cells(tns, b, reverse):
 ENV_SEED = 0
 
 
-def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False):
+def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False, fit_sweeps=0):
     """Bottom environments E[b] of <psi|psi> for b = 1..H (E[H] trivial).
 
     E[b] is stored in column order with sites E[b][c][e, d, dbar, e'] on the
@@ -195,7 +203,8 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False):
         for t in row:                                                # ket: Xc = d, Y = (s, u)
             s, u, l, d, r = t.shape
             mpo.append(np.transpose(t, (2, 3, 0, 1, 4)).reshape(l, d, s * u, r))
-        Z, ls1 = zip_compress(m, mpo, R, seed, philox.STAGE_ENV_KET, b, exact=exact, gram_cut=gram_cut)
+        Z, ls1 = compress(m, mpo, R, seed, philox.STAGE_ENV_KET, b, exact=exact, gram_cut=gram_cut,
+                          fit_sweeps=fit_sweeps)
         # Z_j: k, (s,u), dbar, k' -> bra input: Xc = (s, dbar), Xp = u
         mz, mpo2 = [], []
         for zj, t in zip(Z, row):
@@ -205,7 +214,8 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False):
             mz.append(np.transpose(z5, (0, 1, 3, 2, 4)).reshape(k, s * db, u, kp))
             mpo2.append(np.transpose(t.conj(), (2, 0, 3, 1, 4)).reshape(l, s * d, u, r))
         mz, mpo2 = mirror_mps(mz), list(reversed([np.transpose(w, (3, 1, 2, 0)) for w in mpo2]))
-        Eb, ls2 = zip_compress(mz, mpo2, R, seed, philox.STAGE_ENV_BRA, b, exact=exact, gram_cut=gram_cut)
+        Eb, ls2 = compress(mz, mpo2, R, seed, philox.STAGE_ENV_BRA, b, exact=exact, gram_cut=gram_cut,
+                           fit_sweeps=fit_sweeps)
         Eb = mirror_mps(Eb)                                          # back to column order
         E[b] = [np.transpose(x, (0, 2, 1, 3)) for x in Eb]           # e, u(ket), ubar, e'
         log_norm += ls1 + ls2
@@ -215,7 +225,7 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False):
 
 
 # ------------------------------------------------------------------- sampler
-def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=ORTH_SHIFT, exact=False):
+def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=ORTH_SHIFT, exact=False, fit_sweeps=0):
     """One partition: absorb + compress, right environments, draw left to right.
 
     m: MPS m[a, u, 1, a'] in this row's logical order; row: psi sites in logical
@@ -228,7 +238,7 @@ def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=ORTH
     for t in row:
         s, u, l, d, r = t.shape
         mpo.append(np.transpose(t, (2, 1, 0, 3, 4)).reshape(l, u, s * d, r))
-    Kp, _ = zip_compress(m, mpo, R, seed, philox.STAGE_SAMPLE, b, exact=exact, gram_cut=gram_cut)
+    Kp, _ = compress(m, mpo, R, seed, philox.STAGE_SAMPLE, b, exact=exact, gram_cut=gram_cut, fit_sweeps=fit_sweeps)
     K = [Kp[j].reshape(Kp[j].shape[0], row[j].shape[0], row[j].shape[3], Kp[j].shape[3]) for j in range(W)]
     F = [None] * (W + 1)
     F[W] = np.ones((1, 1, 1), dtype=np.complex128)
@@ -264,13 +274,15 @@ def sample_row(m, row, Eb, R, seed, b, uniforms=None, forced=None, gram_cut=ORTH
     return bits, q0s, logq, m_next
 
 
-def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram_cut=ORTH_SHIFT, exact=False):
+def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram_cut=ORTH_SHIFT, exact=False,
+           fit_sweeps=0):
     """Draw samples (or replay ``forced`` bitstrings); returns bits [n, n_qubits], log q, q0.
 
     q0[n, qubit] is the conditional probability of 0 that the draw of that qubit used.
     """
     H, W = tns.H, tns.W
-    E = env if env is not None else norm_envs(tns, R, ENV_SEED, gram_cut=gram_cut, exact=exact)[0]
+    E = env if env is not None else norm_envs(tns, R, ENV_SEED, gram_cut=gram_cut, exact=exact,
+                                              fit_sweeps=fit_sweeps)[0]
     n = n_samples if forced is None else forced.shape[0]
     bits_out = np.zeros((n, tns.n), dtype=np.uint8)
     q0_out = np.ones((n, tns.n))
@@ -290,7 +302,7 @@ def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram
             else:
                 fb = [int(forced[i, q]) if q >= 0 else 0 for q in qubits]
             xb, q0b, lq, m_next = sample_row(m, row, Eb, R, seed, b, uniforms=uni, forced=fb,
-                                             gram_cut=gram_cut, exact=exact)
+                                             gram_cut=gram_cut, exact=exact, fit_sweeps=fit_sweeps)
             logq[i] += lq
             for j, q in enumerate(qubits):
                 if q >= 0:
@@ -300,7 +312,7 @@ def sample(tns, R, n_samples, seed, sample_offset=0, forced=None, env=None, gram
     return bits_out, logq, q0_out
 
 
-def amplitude(tns, R, bits, seed, gram_cut=ORTH_SHIFT, exact=False):
+def amplitude(tns, R, bits, seed, gram_cut=ORTH_SHIFT, exact=False, fit_sweeps=0):
     """<x|psi> by single-layer boundary MPS over projected rows; returns (log|a|, phase)."""
     H, W = tns.H, tns.W
     m = [np.ones((1, 1, 1, 1), dtype=np.complex128) for _ in range(W)]
@@ -315,7 +327,8 @@ def amplitude(tns, R, bits, seed, gram_cut=ORTH_SHIFT, exact=False):
             q = int(tns.cell_qubit[b, c])
             tp = t[int(bits[q]) if q >= 0 else 0]                       # u, l, d, r
             mpo.append(np.transpose(tp, (1, 0, 2, 3)))                   # l, u, d, r
-        out, ls = zip_compress(m, mpo, R, seed, philox.STAGE_AMPLITUDE, b, exact=exact, gram_cut=gram_cut)
+        out, ls = compress(m, mpo, R, seed, philox.STAGE_AMPLITUDE, b, exact=exact, gram_cut=gram_cut,
+                           fit_sweeps=fit_sweeps)
         if not np.isfinite(ls):
             return -np.inf, 0.0
         log_abs += ls
@@ -389,3 +402,71 @@ def direct_marginals(tns, R, gram_cut=ORTH_SHIFT, exact=False):
                 v = v @ I[cj]
                 ci = cj
     return one, two
+
+
+# ------------------------------------------------- one-site variational fitting
+def _product_site(m, w):
+    """P[a, l, y, xp, a', r] = sum_xc m[a, xc, xp, a'] w[l, xc, y, r] (exact MPS-MPO site)."""
+    return np.einsum("acpA,lcyr->alypAr", m, w)
+
+
+def fit_compress(mps, mpo, R, seed, stage, row, sweeps=2, exact=False, gram_cut=ORTH_SHIFT, history=None):
+    """MPS-MPO compression to rank R by one-site variational fitting (Methods and
+    Appendix "Sampling...": maximise the overlap of the output MPS with the exact
+    MPS-MPO product by sweeping through the output's sites and replacing each with
+    the derivative of the overlap with respect to it; Verstraete, Murg, Cirac 2008).
+
+    The initial guess is the zip-up result (``zip_compress``), so the bond dimensions
+    are those of the zip; each sweep goes right to left then left to right, keeping
+    the output in mixed canonical form around the updated site (QR / LQ of the
+    update; the triangular factor is dropped because the neighbour is recomputed
+    from the environments).  Returns the output in the zip's convention (sites
+    out[k, y, xp, k'], left-isometric except the last, which carries unit norm) and
+    log of the output's norm.  ``history`` (a list) receives the overlap
+    |<Y|P>| / |Y| after every local update.
+    """
+    W = len(mps)
+    Y, _ = zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut)
+    P = [_product_site(m, w) for m, w in zip(mps, mpo)]
+    one = np.ones((1, 1, 1), dtype=np.complex128)
+
+    def grow_left(Lj, j):          # L_{j+1}[k', a', r]
+        return np.einsum("kal,kypK,alypAr->KAr", Lj, Y[j].conj(), P[j], optimize=True)
+
+    def grow_right(Rj1, j):        # R_j[k, a, l]
+        return np.einsum("kypK,alypAr,KAr->kal", Y[j].conj(), P[j], Rj1, optimize=True)
+
+    def update(Lj, Rj1, j):        # derivative of <Y|P> w.r.t. conj(Y_j)
+        return np.einsum("kal,alypAr,KAr->kypK", Lj, P[j], Rj1, optimize=True)
+
+    log_norm = 0.0
+    for _ in range(sweeps):
+        # left environments for the current (left-canonical) guess
+        L = [one]
+        for j in range(W - 1):
+            L.append(grow_left(L[j], j))
+        Rn = [None] * (W + 1)
+        Rn[W] = one
+        for j in range(W - 1, 0, -1):            # right to left
+            Yj = update(L[j], Rn[j + 1], j)
+            if history is not None:
+                history.append(float(np.linalg.norm(Yj)))
+            k, y, xp, kp = Yj.shape
+            q, _r = np.linalg.qr(Yj.reshape(k, y * xp * kp).T)       # Yj = r^T q^T: rows of q^T orthonormal
+            Y[j] = q.T.reshape(q.shape[1], y, xp, kp)
+            Rn[j] = grow_right(Rn[j + 1], j)
+        L = [one]
+        for j in range(W):                       # left to right
+            Yj = update(L[j], Rn[j + 1], j)
+            if history is not None:
+                history.append(float(np.linalg.norm(Yj)))
+            if j == W - 1:
+                nrm = float(np.linalg.norm(Yj))
+                log_norm = float(np.log(nrm)) if nrm > 0 else -np.inf
+                Y[j] = Yj / nrm if nrm > 0 else Yj
+                break
+            k, y, xp, kp = Yj.shape
+            q, _r = np.linalg.qr(Yj.reshape(k * y * xp, kp))
+            Y[j] = q.reshape(k, y, xp, q.shape[1])
+            L.append(grow_left(L[j], j))
+    return Y, log_norm
