@@ -20,7 +20,12 @@ after every application, then an SVD of the projected matrix): the rank-R
 truncation that the library computes.  When R + oversampling covers the full
 column dimension the test matrix is the identity and the step is an exact
 truncated SVD.  ``zip_compress(exact=True)`` takes the plain SVD instead and is
-used to pin the range finder.
+used to pin the range finder.  ``fit_sweeps > 0`` follows the zip with the
+paper's one-site variational fitting (``fit_compress``; Methods and Fig. 7c),
+which only raises the overlap with the exact MPS-MPO product.
+
+``direct_marginals`` gives sample-free one-site and same-row two-site marginals
+from the norm network (top and bottom environments around each row).
 
 Index conventions (logical order j = 0..W-1 along the sweep direction):
   MPS site  m[a, Xc, Xp, a']   (Xc contracted with the MPO, Xp passed through)
