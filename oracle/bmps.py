@@ -475,3 +475,23 @@ def fit_compress(mps, mpo, R, seed, stage, row, sweeps=2, exact=False, gram_cut=
             Y[j] = q.reshape(k, y, xp, q.shape[1])
             L.append(grow_left(L[j], j))
     return Y, log_norm
+
+
+# --------------------------------------------------------- sample certification
+def certify(tns, bits, logq, R_cert, seed=0, bins=20):
+    """p(x) of sampled bitstrings by an independent amplitude contraction at rank
+    R_cert (e.g. twice the sampling rank; Methods "p(x) = |<x|psi>|^2" and the
+    verification step of the Appendix), normalised by <psi|psi> at the same rank.
+
+    Returns dict(log_p, ratio = p/q, mean_ratio (an estimator of 1), kld =
+    E_q[log q - log p], hist = (counts, edges) of log10(p/q)).
+    """
+    _, log_norm = norm_envs(tns, R_cert)
+    log_p = np.array([2.0 * amplitude(tns, R_cert, x, seed)[0] - log_norm for x in np.asarray(bits)])
+    logq = np.asarray(logq, dtype=np.float64)
+    ratio = np.exp(log_p - logq)
+    finite = np.isfinite(log_p)
+    lr = np.log10(ratio[finite & (ratio > 0)])
+    hist = np.histogram(lr, bins=bins) if lr.size else (np.zeros(bins, dtype=np.int64), np.linspace(0, 1, bins + 1))
+    return dict(log_p=log_p, ratio=ratio, mean_ratio=float(ratio.mean()), kld=float(np.mean(logq - log_p)),
+                hist=hist)

@@ -50,3 +50,19 @@ def test_first_site_marginal_equals_first_sampler_conditional():
     _, _, q0 = bmps.sample(t, 64, 1, seed=3)
     q = int(t.cell_qubit[0, 0])
     assert abs(q0[0, q] - (1.0 - one[q])) < 1e-10
+
+
+def test_certification_at_exact_rank_and_unbiased_mean_ratio():
+    """Exact sampling: p/q = 1 for every sample, KLD 0.  Truncated sampling: the mean of
+    p/q estimates sum_x p(x) = 1 (Methods) within 4 standard errors."""
+    lat = w.square(3, 3)
+    bits = w.domain_wall_bits(lat)
+    t = _state(lat, bits, w.random_su4_circuit(lat, 1, seed=4), 16)
+    xs, lq, _ = bmps.sample(t, 64, 30, seed=2)
+    c = bmps.certify(t, xs, lq, 64)
+    assert np.allclose(c["ratio"], 1.0, atol=1e-9) and abs(c["kld"]) < 1e-9
+    xs, lq, _ = bmps.sample(t, 2, 300, seed=3)
+    c = bmps.certify(t, xs, lq, 64)
+    r = c["ratio"]
+    assert abs(r.mean() - 1.0) < 4 * r.std() / np.sqrt(r.size)
+    assert c["kld"] > -0.05 and sum(c["hist"][0]) == r.size
