@@ -64,6 +64,17 @@ tns_status tns_test_contract(const char* labels_a, const int64_t* dims_a, const 
                              int32_t conj_b, const void* B_dev, const char* labels_c, const int64_t* dims_c,
                              const int64_t* strides_c, void* C_dev, int32_t mode, void* cuda_stream);
 
+/* The contraction planner's decision for tns_test_contract's mode 1 (tensor cores),
+ * computed on the host without touching a device (operand pointers are not
+ * needed).  out (host int64 [11]): [0] 1 = tensor cores, 0 = CUDA cores (too small
+ * or not expressible); [1] operand roles swapped (C^T = B^T A^T); [2] the A-side
+ * operand read in place; [3] / [4] A / B side shared by every batch entry; [5] batch
+ * rows merged into one launch; [6] tile width in real columns (128 or 256); [7] M,
+ * [8] N (complex, after any swap); [9] K; [10] batch entries. */
+tns_status tns_test_plan(const char* labels_a, const int64_t* dims_a, const int64_t* strides_a, int32_t conj_a,
+                         const char* labels_b, const int64_t* dims_b, const int64_t* strides_b, int32_t conj_b,
+                         const char* labels_c, const int64_t* dims_c, const int64_t* strides_c, int64_t* out);
+
 /* Batched FP64 thin SVD A = U diag(s) V^H (m >= n) by one-sided Jacobi.
  *   A_dev  device complex128 [batch][m][n] (read only); s_dev float64 [batch][n];
  *   U_dev  complex128 [batch][m][n]; V_dev complex128 [batch][n][n] */

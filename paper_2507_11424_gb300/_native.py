@@ -62,6 +62,8 @@ SIGNATURES = {
     "tns_test_contract": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_char_p, C.c_void_p,
                                     C.c_void_p, C.c_int32, C.c_void_p, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_int32, C.c_void_p]),
+    "tns_test_plan": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p, C.c_void_p,
+                                C.c_int32, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_test_svd": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     "tns_last_error": (C.c_char_p, []),

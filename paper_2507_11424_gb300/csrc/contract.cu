@@ -416,7 +416,7 @@ static bool dense_a(const GemmParams& p) {
 
 struct TcRole {
   GemmParams q;
-  bool a_sh, b_sh, ad, ok;
+  bool a_sh, b_sh, ad, ok, swapped;
   double cost;   // bytes written by the operand packing
 };
 
@@ -427,6 +427,7 @@ struct TcRole {
 static TcRole tc_role(const GemmParams& p, long long nbatch, bool swapped) {
   TcRole r;
   r.q = p;
+  r.swapped = swapped;
   if (swapped) swap_roles(r.q);
   GemmParams& q = r.q;
   sort_groups(q.nk, q.kdim, q.sAk, q.sBk, nullptr);
@@ -442,22 +443,38 @@ static TcRole tc_role(const GemmParams& p, long long nbatch, bool swapped) {
   return r;
 }
 
+// The role assignment the tensor-core path uses (the cheaper packing of the two),
+// or false when neither fits the kernel (both operands shared across a batch, or
+// more rows than a TMA coordinate holds).
+static bool pick_role(const GemmParams& p0, long long nbatch, TcRole& r) {
+  if (p0.M < 1 || p0.N < 1 || p0.K < 1) return false;
+  const TcRole r0 = tc_role(p0, nbatch, false), r1 = tc_role(p0, nbatch, true);
+  if (!r0.ok && !r1.ok) return false;
+  r = (!r0.ok || (r1.ok && r1.cost < r0.cost)) ? r1 : r0;
+  const long long rowsA = (r.a_sh ? 1 : nbatch) * r.q.M, rowsB = (r.b_sh ? 1 : nbatch) * 2LL * r.q.N;
+  return rowsA + 128 < (1LL << 31) && rowsB + 256 < (1LL << 31);
+}
+
+// Whether a contraction of this size goes to the tensor cores (else the SIMT kernel).
+static bool tc_worth_it(const GemmParams& p, long long nbatch) {
+  const double macs = (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
+  return macs >= 16777216.0 && p.K >= 8;
+}
+
 // Run the contraction on the tensor cores.  *handled = false (and nothing
 // launched) when the contraction does not fit the kernel.
 static cudaError_t contract_tc(const GemmParams& p0, long long nbatch, cudaStream_t st, ContractTiming* tm,
                                bool* handled) {
   *handled = false;
-  if (!tc_available() || p0.M < 1 || p0.N < 1 || p0.K < 1) return cudaSuccess;
-  const TcRole r0 = tc_role(p0, nbatch, false), r1 = tc_role(p0, nbatch, true);
-  if (!r0.ok && !r1.ok) return cudaSuccess;
-  const TcRole& r = (!r0.ok || (r1.ok && r1.cost < r0.cost)) ? r1 : r0;
+  if (!tc_available()) return cudaSuccess;
+  TcRole r;
+  if (!pick_role(p0, nbatch, r)) return cudaSuccess;
   const GemmParams& p = r.q;
   const bool a_sh = r.a_sh, b_sh = r.b_sh, ad = r.ad;
   const int Kr = 2 * p.K;
   const int Kp = (Kr + 31) / 32 * 32;
   const long long nbA = a_sh ? 1 : nbatch, nbB = b_sh ? 1 : nbatch;
   const long long rowsA = nbA * p.M, rowsB = nbB * 2LL * p.N;
-  if (rowsA + 128 >= (1LL << 31) || rowsB + 256 >= (1LL << 31)) return cudaSuccess;
   TcArgs a{};
   a.e.C = (float2*)p.C;
   a.e.M = p.M;
@@ -542,9 +559,12 @@ std::vector<Grp> merge(std::vector<Grp> g, int nops) {
 }
 }  // namespace
 
-cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st, double2 alpha,
-                     double2 beta, double* flops_out, ContractTiming* timing) {
-  if (flops_out) *flops_out = 0.0;
+// Label analysis of C = alpha sum A B + beta C: batch / M / N / K index groups
+// (contiguous runs merged), their strides in each operand, and per-batch offsets.
+// *empty = true when the contraction or its output is empty (nothing to launch).
+static cudaError_t plan_params(const TView& A, const TView& B, const TView& C, double2 alpha, double2 beta,
+                               GemmParams& p, long long& nbatch, bool* empty) {
+  *empty = false;
   std::vector<Lab> labs;
   auto find = [&](char c) -> Lab& {
     for (auto& l : labs)
@@ -578,7 +598,7 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
   std::vector<char> gb_idx_lab;
   long long Mtot = 1, Ntot = 1, Ktot = 1;
   for (auto& l : labs) {
-    if (l.d == 0) return cudaSuccess;  // empty contraction or empty output
+    if (l.d == 0) { *empty = true; return cudaSuccess; }  // empty contraction or empty output
     bool idxl = (l.c == a_idx_label || l.c == b_idx_label || off_labels.find(l.c) != std::string::npos);
     if (l.d == 1 && !idxl) continue;
     if (l.inA && l.inB && l.inC) {
@@ -604,7 +624,7 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
             gk.size(), batch.size(), A.labels.c_str(), B.labels.c_str(), C.labels.c_str());
     return cudaErrorInvalidValue;
   }
-  GemmParams p{};
+  p = GemmParams{};
   p.M = Mtot;
   p.N = (int)Ntot;
   p.K = (int)Ktot;
@@ -616,7 +636,7 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
   for (int i = 0; i < p.nm; ++i) { p.mdim[i] = (int)gm[i].d; p.sAm[i] = gm[i].s0; p.sCm[i] = gm[i].s1; }
   for (int i = 0; i < p.nn; ++i) { p.ndim[i] = (int)gn[i].d; p.sBn[i] = gn[i].s0; p.sCn[i] = gn[i].s1; }
   for (int i = 0; i < p.nk; ++i) { p.kdim[i] = (int)gk[i].d; p.sAk[i] = gk[i].s0; p.sBk[i] = gk[i].s1; }
-  long long nbatch = 1;
+  nbatch = 1;
   for (int i = 0; i < p.nb; ++i) {
     p.bdim[i] = (int)batch[i].d;
     p.sCb[i] = batch[i].s0;
@@ -660,13 +680,23 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
     }
     p.b_kfast = (p.sBk[0] == 1 && !(p.nn > 0 && p.sBn[0] == 1));
   }
-  if (p.M == 0 || p.N == 0) return cudaSuccess;
+  if (p.M == 0 || p.N == 0) *empty = true;
+  return cudaSuccess;
+}
+
+cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, cudaStream_t st, double2 alpha,
+                     double2 beta, double* flops_out, ContractTiming* timing) {
+  if (flops_out) *flops_out = 0.0;
+  GemmParams p{};
+  long long nbatch = 1;
+  bool empty = false;
+  cudaError_t pe = plan_params(A, B, C, alpha, beta, p, nbatch, &empty);
+  if (pe != cudaSuccess || empty) return pe;
   if (flops_out) *flops_out = 8.0 * (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
   if (prec == Prec::TF32X3) {
     // small contractions stay on the SIMT kernel (packing and tile waste dominate)
-    const double macs = (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
     const bool force = timing && timing->force_tc;
-    if (p.beta_zero && alpha.x == 1.0 && alpha.y == 0.0 && (force || (macs >= 16777216.0 && p.K >= 8))) {
+    if (p.beta_zero && alpha.x == 1.0 && alpha.y == 0.0 && (force || tc_worth_it(p, nbatch))) {
       bool handled = false;
       cudaError_t e = contract_tc(p, nbatch, st, timing, &handled);
       if (handled || e != cudaSuccess) return e;
@@ -710,6 +740,31 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
     cudaFreeAsync(p.partial, st);
   }
   return cudaGetLastError();
+}
+
+cudaError_t contract_plan(const TView& A, const TView& B, const TView& C, long long* out) {
+  for (int i = 0; i < 11; ++i) out[i] = 0;
+  GemmParams p{};
+  long long nbatch = 1;
+  bool empty = false;
+  cudaError_t e = plan_params(A, B, C, make_double2(1.0, 0.0), make_double2(0.0, 0.0), p, nbatch, &empty);
+  if (e != cudaSuccess || empty) return e;
+  out[7] = p.M;
+  out[8] = p.N;
+  out[9] = p.K;
+  out[10] = nbatch;
+  TcRole r;
+  if (!tc_worth_it(p, nbatch) || !pick_role(p, nbatch, r)) return cudaSuccess;
+  out[0] = 1;
+  out[1] = r.swapped ? 1 : 0;
+  out[2] = r.ad;
+  out[3] = r.a_sh;
+  out[4] = r.b_sh;
+  out[5] = (r.b_sh && !r.a_sh) ? 1 : 0;
+  out[6] = tc_tile_n(r.q.N);
+  out[7] = r.q.M;
+  out[8] = r.q.N;
+  return cudaSuccess;
 }
 
 }  // namespace tns

@@ -56,6 +56,13 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
                      double2 alpha = make_double2(1.0, 0.0), double2 beta = make_double2(0.0, 0.0),
                      double* flops_out = nullptr, ContractTiming* timing = nullptr);
 
+// The planner's decision for a contraction in the TF32X3 precision, without
+// launching anything (host only): out[0] tensor cores used (1) or CUDA cores (0),
+// [1] operand roles swapped, [2] A read in place, [3] A shared by the batch, [4] B
+// shared, [5] batch rows merged into one launch, [6] tile width in real columns,
+// [7] M, [8] N (complex, after any swap), [9] K, [10] batch entries.
+cudaError_t contract_plan(const TView& A, const TView& B, const TView& C, long long* out);
+
 // Number of GEMM launches issued so far (for launch accounting).
 long long contract_launches();
 

@@ -414,7 +414,7 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
 
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st) {
   if (!tc_available() || a.e.M < 1 || a.e.N < 1 || a.Kr < 1 || a.nbatch < 1) return cudaErrorNotSupported;
-  if (2LL * a.e.N <= 128) return launch_bn<128>(op, a, st);
+  if (tc_tile_n(a.e.N) == 128) return launch_bn<128>(op, a, st);
   return launch_bn<256>(op, a, st);
 }
 

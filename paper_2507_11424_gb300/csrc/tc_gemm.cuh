@@ -59,6 +59,9 @@ __host__ __device__ inline float tf32_rn(float x) {
 #endif
 }
 
+// Tile width (real output columns) for an output of n complex columns.
+inline int tc_tile_n(long long n_complex) { return 2 * n_complex <= 128 ? 128 : 256; }
+
 bool tc_available();
 // cudaErrorNotSupported when the shape or alignment does not fit the kernel.
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st);

@@ -192,3 +192,30 @@ extern "C" tns_status tns_test_contract(const char* labels_a, const int64_t* dim
   }
   return TNS_OK;
 }
+
+extern "C" tns_status tns_test_plan(const char* labels_a, const int64_t* dims_a, const int64_t* strides_a,
+                                    int32_t conj_a, const char* labels_b, const int64_t* dims_b,
+                                    const int64_t* strides_b, int32_t conj_b, const char* labels_c,
+                                    const int64_t* dims_c, const int64_t* strides_c, int64_t* out) {
+  if (!labels_a || !labels_b || !labels_c || !dims_a || !dims_b || !dims_c || !strides_a || !strides_b ||
+      !strides_c || !out) {
+    set_error("invalid argument");
+    return TNS_ERR_ARG;
+  }
+  auto mk = [](const char* lab, const int64_t* d, const int64_t* st, int cj) {
+    TView v;
+    v.labels = lab;
+    for (size_t i = 0; i < v.labels.size(); ++i) {
+      v.dim.push_back(d[i]);
+      v.stride.push_back(st[i]);
+    }
+    v.conj = cj != 0;
+    return v;
+  };
+  long long o[11];
+  cudaError_t e = contract_plan(mk(labels_a, dims_a, strides_a, conj_a), mk(labels_b, dims_b, strides_b, conj_b),
+                                mk(labels_c, dims_c, strides_c, 0), o);
+  if (e != cudaSuccess) { set_error("inconsistent contraction views"); return TNS_ERR_ARG; }
+  for (int i = 0; i < 11; ++i) out[i] = o[i];
+  return TNS_OK;
+}
