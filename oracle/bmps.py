@@ -25,7 +25,9 @@ paper's one-site variational fitting (``fit_compress``; Methods and Fig. 7c),
 which only raises the overlap with the exact MPS-MPO product.
 
 ``direct_marginals`` gives sample-free one-site and same-row two-site marginals
-from the norm network (top and bottom environments around each row).
+from the norm network (top and bottom environments around each row);
+``projected_marginal`` gives <prod n_q> for any set of qubits as the norm of the
+projected state over the norm of the state.
 
 Index conventions (logical order j = 0..W-1 along the sweep direction):
   MPS site  m[a, Xc, Xp, a']   (Xc contracted with the MPO, Xp passed through)
@@ -495,3 +497,22 @@ def certify(tns, bits, logq, R_cert, seed=0, bins=20):
     hist = np.histogram(lr, bins=bins) if lr.size else (np.zeros(bins, dtype=np.int64), np.linspace(0, 1, bins + 1))
     return dict(log_p=log_p, ratio=ratio, mean_ratio=float(ratio.mean()), kld=float(np.mean(logq - log_p)),
                 hist=hist)
+
+
+def projected_marginal(tns, R, qubits, gram_cut=ORTH_SHIFT, exact=False):
+    """<prod_q n_q> = |prod_q P1_q psi|^2 / |psi|^2 for the given qubits (any rows): the
+    norm network of the state with those qubits' physical index fixed to 1, over
+    the norm network of the state (both at boundary rank R)."""
+    class _Proj:
+        pass
+    proj = _Proj()
+    proj.H, proj.W = tns.H, tns.W
+    proj.T = [[t for t in row] for row in tns.T]
+    for q in qubits:
+        r, c = (int(x) for x in np.argwhere(tns.cell_qubit == q)[0])
+        t = tns.T[r][c].copy()
+        t[0] = 0.0
+        proj.T[r][c] = t
+    _, ln_p = norm_envs(proj, R, gram_cut=gram_cut, exact=exact)
+    _, ln = norm_envs(tns, R, gram_cut=gram_cut, exact=exact)
+    return float(np.exp(ln_p - ln)) if np.isfinite(ln_p) else 0.0

@@ -66,3 +66,20 @@ def test_certification_at_exact_rank_and_unbiased_mean_ratio():
     r = c["ratio"]
     assert abs(r.mean() - 1.0) < 4 * r.std() / np.sqrt(r.size)
     assert c["kld"] > -0.05 and sum(c["hist"][0]) == r.size
+
+
+def test_projected_norms_agree_with_row_transfers_and_bruteforce():
+    """Two independent contractions of the same marginals: the norm of the projected
+    state (any pair of rows) and the row transfer between top and bottom environments
+    (same row); both against brute force."""
+    lat = w.square(3, 3)
+    bits = w.domain_wall_bits(lat)
+    t = _state(lat, bits, w.random_su4_circuit(lat, 1, seed=11), 16)
+    one, two = bmps.direct_marginals(t, 64)
+    o_ref, t_ref = metrics.marginals_from_statevector(t.statevector_bruteforce())
+    q_same = [int(t.cell_qubit[1, 0]), int(t.cell_qubit[1, 2])]
+    q_cross = [int(t.cell_qubit[0, 1]), int(t.cell_qubit[2, 2])]
+    assert abs(bmps.projected_marginal(t, 64, [q_same[0]]) - one[q_same[0]]) < 1e-10
+    assert abs(bmps.projected_marginal(t, 64, q_same) - two[q_same[0], q_same[1]]) < 1e-10
+    assert abs(bmps.projected_marginal(t, 64, q_cross) - t_ref[q_cross[0], q_cross[1]]) < 1e-10
+    assert np.isnan(two[q_cross[0], q_cross[1]])
