@@ -37,8 +37,8 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s SIMT FP32
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tf32 : bf16 tensor throughput
 # DRAM traffic of the tensor-core GEMM kernel from one ncu capture of a smaller case of the
-# same contraction (A 32768 x 1024 complex64 read once, B 1024 x 1024, C 32768 x 1024;
-# profiles/tc_gemm_tf32x3_M32768_N1024_K1024.md): dram read + write bytes and the case's
+# same contraction (A 32768 x 1024 complex64 read once, B 1024 x 1024, C 32768 x 1024; the
+# `--gemm-case 32768,1024,1024` mode of this script): dram read + write bytes and the case's
 # algorithmic flop.  Traffic grows with the rows processed, so a launch's traffic is scaled
 # by its flop.
 TC_CAPTURE_BYTES = 418.606848e6 + 244.045568e6
@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--gemm-case", default=None, metavar="M,N,K",
+                    help="time one tensor-core complex GEMM C = A B^T of this shape instead (profiling case)")
+    ap.add_argument("--gemm-reps", type=int, default=2)
     ap.add_argument("--state-cache", default=None,
                     help="TNSF file: load the state from it when present, else build it and save it there")
     return ap.parse_args()
@@ -389,8 +392,40 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gemm_case(args):
+    """One tensor-core complex contraction C = A B^T (A complex64 [M][K], B [N][K], random)
+    through tns_test_tcgemm (B expansion, then the GEMM kernel), timed with CUDA events;
+    prints the mean time per call after the first and the algorithmic rate 8 M N K / t."""
+    import ctypes as C
+    import torch
+    from paper_2507_11424_gb300 import build, _native
+    M, N, K = (int(x) for x in args.gemm_case.split(","))
+    build.build()
+    lib = _native.load()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((M, 2 * K), device="cuda", generator=g)
+    B = torch.randn((N, 2 * K), device="cuda", generator=g)
+    Cm = torch.empty((M, 2 * N), device="cuda")
+    times = []
+    for _ in range(max(1, args.gemm_reps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc = lib.tns_test_tcgemm(M, N, K, C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                                 C.c_void_p(Cm.data_ptr()), None)
+        e1.record()
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise SystemExit(f"tns_test_tcgemm failed: {lib.tns_last_error().decode()}")
+        times.append(e0.elapsed_time(e1))
+    ms = sum(times[1:]) / (len(times) - 1) if len(times) > 1 else times[0]
+    print(json.dumps({"gemm_case": [M, N, K], "ms_per_call": ms, "tflops": 8.0 * M * N * K / (ms / 1e3) / 1e12}))
+
+
 def main():
     args = parse()
+    if args.gemm_case:
+        run_gemm_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

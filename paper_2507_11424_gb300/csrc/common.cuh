@@ -70,3 +70,13 @@ __host__ __device__ inline double u53(uint32_t hi, uint32_t lo) {
 enum { STAGE_SAMPLE = 0, STAGE_ENV_KET = 1, STAGE_ENV_BRA = 2, STAGE_AMPLITUDE = 3 };
 
 #define TNS_CUDA_OK(x) ((x) == cudaSuccess)
+
+namespace tns {
+// Unique id of the CUDA context current on this thread (binding the device's
+// primary context first).  Ids are never reused within a process, so a cache
+// keyed by it goes stale neither across devices nor across cudaDeviceReset.
+cudaError_t current_context_id(unsigned long long* id);
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) once per context
+// (thread-safe); later calls with the same (context, fn, bytes) return at once.
+cudaError_t smem_optin(const void* fn, int bytes);
+}  // namespace tns

@@ -369,14 +369,12 @@ cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double s
   size_t bytes = (size_t)2 * n * n * (f32 ? sizeof(cf) : sizeof(cd));
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(chol_w_kernel<cd, cd, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    cudaFuncSetAttribute(chol_w_kernel<cf, cd, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    cudaFuncSetAttribute(chol_w_kernel<cf, cf, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    attr = true;
-  }
   const size_t sm = use_smem ? bytes : 0;
+  cudaError_t ea = cudaSuccess;
+  if (w_f64 && g_f64) ea = smem_optin((const void*)chol_w_kernel<cd, cd, double>, (int)SMEM_LIMIT);
+  else if (g_f64) ea = smem_optin((const void*)chol_w_kernel<cf, cd, double>, (int)SMEM_LIMIT);
+  else if (f32) ea = smem_optin((const void*)chol_w_kernel<cf, cf, float>, (int)SMEM_LIMIT);
+  if (ea != cudaSuccess) return ea;
   if (w_f64 && g_f64)
     chol_w_kernel<cd, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, (cd*)work, use_smem);
   else if (g_f64)
@@ -398,11 +396,8 @@ cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double*
   size_t bytes = (size_t)2 * np * np * sizeof(cd);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(eigh_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    attr = true;
-  }
+  cudaError_t ea = smem_optin((const void*)eigh_kernel<double>, (int)SMEM_LIMIT);
+  if (ea != cudaSuccess) return ea;
   eigh_kernel<double><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
                                                                         use_smem, sweeps_out);
   return cudaGetLastError();
@@ -416,14 +411,16 @@ cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batc
   size_t bytes = (size_t)2 * np * np * sizeof(cf);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(eigh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    attr = true;
-  }
+  cudaError_t ea = smem_optin((const void*)eigh_kernel<float>, (int)SMEM_LIMIT);
+  if (ea != cudaSuccess) return ea;
   eigh_kernel<float><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
                                                                        use_smem, sweeps_out);
   return cudaGetLastError();
+}
+
+bool eigh_fits_smem(int n) {
+  size_t np = n + (n & 1);
+  return (size_t)2 * np * np * sizeof(cd) <= SMEM_LIMIT;
 }
 
 bool jacobi_fits_smem_f32(int n) {
@@ -439,11 +436,8 @@ cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, d
   size_t bytes = ((size_t)m * np + (size_t)np * np) * sizeof(cd);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
-    attr = true;
-  }
+  cudaError_t ea = smem_optin((const void*)svd_kernel, (int)SMEM_LIMIT);
+  if (ea != cudaSuccess) return ea;
   svd_kernel<<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, m, n, sigma, U, sU, V, sV, work, status,
                                                               use_smem);
   return cudaGetLastError();

@@ -40,7 +40,9 @@ bool chol_fits_smem(int n);
 cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, double* sigma, cd* U, long long sU,
                         cd* V, long long sV, cd* work, int* status, cudaStream_t st);
 
-// Largest batch of n-sized problems that eigh/svd can run from shared memory.
+// Whether svd_batched of an m x n matrix runs from shared memory (else it needs work).
 bool jacobi_fits_smem(int m, int n);
+// Whether eigh_batched of an n x n matrix runs from shared memory (else it needs work).
+bool eigh_fits_smem(int n);
 
 }  // namespace tns

@@ -7,6 +7,7 @@
 // runs the library's FP64 Jacobi eigensolver with its scratch (the working copy
 // of matrices too large for shared memory, and the per-matrix status words) in
 // a file-scope device array instead of allocated memory.
+#include <map>
 #include <mutex>
 
 #include "../../include/tns.h"
@@ -19,28 +20,27 @@ namespace tns {
 static constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Device addresses of the array, looked up once per device.  In host code the
-// symbol name is only a host-side stand-in: the kernel must receive the address
-// that cudaGetSymbolAddress returns for the current device.
-static constexpr int MAX_DEVICES = 64;
-static void* g_scratch_addr[MAX_DEVICES] = {};
+// Device addresses of the array, looked up once per CUDA context with its device
+// current.  In host code the symbol name is only a host-side stand-in: the kernel
+// must receive the address that cudaGetSymbolAddress returns.  The cache is keyed
+// by the context's unique id, so a second device, or the same device after
+// cudaDeviceReset (new primary context, module loaded again, possibly at another
+// address), looks the address up again instead of reusing a stale one.
+static std::map<unsigned long long, void*> g_scratch_addr;
 static std::mutex g_scratch_mu;
 
 static tns_status scratch_address(void** out) {
-  int dev = -1;
-  TNS_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAX_DEVICES) {
-    set_error("tns_eigh_noalloc: device ordinal %d not supported", dev);
-    return TNS_ERR_ARG;
-  }
+  unsigned long long ctx = 0;
+  TNS_TRY_CUDA(current_context_id(&ctx));
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  auto it = g_scratch_addr.find(ctx);
+  if (it == g_scratch_addr.end()) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_scratch_addr[dev] = p;
+    it = g_scratch_addr.emplace(ctx, p).first;
   }
-  *out = g_scratch_addr[dev];
+  *out = it->second;
   return TNS_OK;
 }
 
@@ -59,7 +59,7 @@ extern "C" tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A
   if (batch == 0) return TNS_OK;
   const size_t np = (size_t)n + (n & 1);
   const size_t status_bytes = align256(sizeof(int) * (size_t)batch);
-  const size_t work_bytes = jacobi_fits_smem(n, n) ? 0 : (size_t)batch * 2 * np * np * sizeof(cd);
+  const size_t work_bytes = eigh_fits_smem(n) ? 0 : (size_t)batch * 2 * np * np * sizeof(cd);
   if (status_bytes + work_bytes > NOALLOC_SCRATCH_BYTES) {
     set_error("tns_eigh_noalloc: batch %d of %dx%d matrices needs %zu bytes of scratch, above the %zu-byte "
               "static limit",

@@ -600,7 +600,7 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(B, "Sne", {S, N, kk}, true), view(B, "Snf", {S, N, kk}),
                            view(Hm, "Sef", {S, kk, kk}), cx.gp));
     cd* work = nullptr;
-    if (!jacobi_fits_smem(kk, kk)) TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
+    if (!eigh_fits_smem(kk)) TNS_TRY(wsget(s, "z_jwork", sizeof(cd) * S * 2 * np * np, (void**)&work));
     TNS_TRY_CUDA(peigh(s, Hm, kk, (int)S, mu, V, work, status));
   } else {
     void* H32;

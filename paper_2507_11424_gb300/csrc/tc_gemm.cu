@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -394,12 +395,9 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
   if (!make_map(&ma, op.A, rowsA, a.Kr, op.lda, BM) || !make_map(&mbhi, op.Bhi, rowsB, a.Kr, op.ldb, BN) ||
       !make_map(&mblo, op.Blo, rowsB, a.Kr, op.ldb, BN))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM);
+  {
+    cudaError_t e = smem_optin((const void*)tc_gemm_tf32x3_kernel<BN>, (int)SMEM);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   a.tiles_n = (int)((2LL * a.e.N + BN - 1) / BN);
   const long long mrows = a.merged ? a.nbatch * a.e.M : a.e.M;
@@ -419,18 +417,19 @@ cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t s
 }
 
 int* tc_error_flag() {
-  static int* flags[64] = {};
+  // one flag per CUDA context (a new context after cudaDeviceReset gets a new flag)
+  static std::map<unsigned long long, int*> flags;
   static std::mutex mu;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  unsigned long long ctx = 0;
+  if (current_context_id(&ctx) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  if (!flags[dev]) {
-    int* f = nullptr;
-    if (cudaMalloc(&f, sizeof(int)) != cudaSuccess) return nullptr;
-    if (cudaMemset(f, 0, sizeof(int)) != cudaSuccess) { cudaFree(f); return nullptr; }
-    flags[dev] = f;
-  }
-  return flags[dev];
+  auto it = flags.find(ctx);
+  if (it != flags.end()) return it->second;
+  int* f = nullptr;
+  if (cudaMalloc(&f, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(f, 0, sizeof(int)) != cudaSuccess) { cudaFree(f); return nullptr; }
+  flags[ctx] = f;
+  return f;
 }
 
 }  // namespace tns

@@ -40,7 +40,7 @@ extern "C" tns_status tns_test_eigh(int32_t batch, int32_t n, const double* A, d
   int* sweeps = nullptr;
   TNS_TRY_CUDA(cudaMalloc(&status, sizeof(int) * (batch > 0 ? batch : 1)));
   TNS_TRY_CUDA(cudaMalloc(&sweeps, sizeof(int) * (batch > 0 ? batch : 1)));
-  if (!jacobi_fits_smem(n, n)) {
+  if (!eigh_fits_smem(n)) {
     long long np = n + (n & 1);
     TNS_TRY_CUDA(cudaMalloc(&work, sizeof(cd) * batch * 2 * np * np));
   }

@@ -121,7 +121,7 @@ def _tree_lattice(H, W):
 
 @pytest.mark.parametrize("shape", [(1, 6), (3, 3)])
 def test_discarded_weight_exact_on_trees(shape):
-    """Without loops BP is exact, so <psi|psi> = prod_i (1 - eps_i) (Eqs. 1-2, L83 remark)."""
+    """Without loops BP is exact, so <psi|psi> = prod_i (1 - eps_i) (Eqs. 1-2 and the remark after them)."""
     H, W = shape
     lat = w.square(H, W) if H == 1 else _tree_lattice(H, W)
     bits = (np.arange(lat.n_qubits) % 2).astype(np.uint8)
@@ -139,7 +139,7 @@ def test_discarded_weight_exact_on_trees(shape):
 
 
 def test_bp_messages_are_exact_environments_on_tree():
-    """On a tree the BP fixed point equals the exact environment of the cut bond (L78).
+    """On a tree the BP fixed point equals the exact environment of the cut bond (Methods, BP on trees).
 
     The message into (0,0) from (0,1) must equal the contraction of the branch
     {(0,1), (0,2)} of <psi|psi> with the cut bond left open.
