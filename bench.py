@@ -62,8 +62,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "learned"],
+                    help="plain: the boundary-MPS sampler; learned: MADE proposal + independent MH on the same state")
+    ap.add_argument("--train-samples", type=int, default=32768)
+    ap.add_argument("--train-chib", type=int, default=16,
+                    help="boundary rank of the plain-sampler draws the network is trained on")
+    ap.add_argument("--proposals", type=int, default=8192)
+    ap.add_argument("--chains", type=int, default=128)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-samples", type=int, default=8,
+                    help="samples the plain FP64 sampler replays for its rate and the marginal error (0 = skip)")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--gemm-case", default=None, metavar="M,N,K",
                     help="time one tensor-core complex GEMM C = A B^T of this shape instead (profiling case)")
@@ -216,6 +225,42 @@ def finish_cpu_baseline(p, q, path, timeout):
 
 
 # ---------------------------------------------------------------- GPU arm
+def plain_sampler(st, R, args, seed0):
+    """The plain FP64 sampler on the same state: its rate, and the marginal error of the
+    mixed path against it.
+
+    The mixed path draws `--plain-samples` samples with their conditionals; the FP64 path
+    (every contraction and factorisation in FP64) then replays the same bitstrings
+    (forced-path replay, the same work as drawing them) and is timed with CUDA events
+    after a one-sample warm-up.  The marginal error is max / mean |q_mixed - q_fp64| over
+    every conditional q(x_v = 0 | prefix) of those samples.
+    """
+    import torch
+    n = args.plain_samples
+    xs, _, cond_m = st.sample(R, n, seed0 + 300, cond=True)
+    st.set_precision("fp64")
+    try:
+        t0 = time.time()
+        st.log_norm(R)                            # FP64 norm environments (setup, as for the mixed path)
+        env_s = time.time() - t0
+        st.sample_replay(R, xs[:1])               # warm-up
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, cond_p = st.sample_replay(R, xs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        st.set_precision(args.prec)
+    d = (cond_m - cond_p).abs()
+    return {"samples_per_s": n / (ms / 1e3), "samples": n, "ms": ms, "env_build_s": round(env_s, 2),
+            "marginal_err_max": float(d.max()), "marginal_err_mean": float(d.mean()),
+            "what": ("TNS_PREC_FP64 replay of the mixed path's bitstrings (same work as drawing them), CUDA events; "
+                     "marginal error = |q_mixed - q_fp64| over every conditional of those samples")}
+
+
 def run_gpu(args):
     import torch
     import paper_2507_11424_gb300 as pkg
@@ -292,6 +337,7 @@ def run_gpu(args):
     e2e_s = time.time() - t0
     e2e_s = max_over_ranks(e2e_s, world)
     sector = float((bits_h.numpy().sum(axis=1) == int(bits.sum())).mean())
+    plain = plain_sampler(st, R, args, seed0) if args.prec == "mixed" and args.plain_samples > 0 else None
     env = prof["env_gemm"]
     achieved = env["flops"] / (env["ms"] / 1e3) / 1e12 if env["ms"] > 0 else None
     total_flops = sum(v["flops"] for v in prof.values())
@@ -329,6 +375,7 @@ def run_gpu(args):
         "profile": {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
                         "tflops": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 2) if v["ms"] > 0 and v["flops"] else None}
                     for k, v in prof.items() if v["launches"]},
+        "plain_fp64": plain,
         "state_build_s": round(build_s, 2), "env_build_s": round(env_s, 3), "log_norm": log_norm,
         "log_fidelity": st.log_fidelity(), "sector_fraction": sector,
     }
@@ -337,6 +384,114 @@ def run_gpu(args):
     st.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- learned proposal
+def marginals(bits):
+    """One-site means and same-sample two-site means <x_i x_j> of a [N][n] bit array."""
+    import numpy as np
+    x = np.asarray(bits, dtype=np.float64)
+    return x.mean(0), (x.T @ x) / x.shape[0]
+
+
+def run_learned(args):
+    """The learned-proposal sampler on the 10x10 state (independent MH with a MADE proposal).
+
+    Steps, on one GPU, all through the library: (1) plain-sampler draws at boundary rank
+    --train-chib as training data; (2) MADE training (4 weight layers, hidden 256, BF16
+    tensor-core GEMMs, Adam, 20 epochs); (3) --proposals ancestral proposals and their
+    log g; (4) log p = 2 log|<x|psi>| at chi_b = 64 for every proposal (tns_amplitude);
+    (5) --chains independent MH chains over the proposals, started from plain-sampler
+    draws.  Timed (CUDA events): the sampling stage (3)-(5) against the plain mixed
+    sampler at chi_b = 64 drawing the reference samples on the same state; training
+    (1)-(2) is reported separately (paid once per state).  Marginal quality: TVD-style
+    maximum distance of one- and two-site marginals of the chain states from the plain
+    sampler's, with the plain sampler's shot noise beside it.
+    """
+    import numpy as np
+    import torch
+    import paper_2507_11424_gb300 as pkg
+    import workloads as w
+    torch.cuda.set_device(0)
+    cfg, lat, bits, groups = workload()
+    chi, R, n = cfg["chi"], cfg["chi_b"], lat.n_qubits
+    t0 = time.time()
+    if args.state_cache and os.path.exists(args.state_cache):
+        st = pkg.TNSState.load_file(args.state_cache)
+        st.n = n
+        st.set_precision("mixed")
+    else:
+        st = pkg.TNSState(lat.grid_rc, lat.edges, bits, chi_max=chi, prec="mixed")
+        for g in groups:
+            st.apply_gate_layer(g, chi=chi)
+            st.bp_gauge(300, 1e-10)
+        if args.state_cache:
+            st.save(args.state_cache)
+    build_s = time.time() - t0
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    st.log_norm(R)
+    st.log_norm(args.train_chib)
+    # plain sampler at chi_b = 64: the reference draws and the rate to beat
+    (ref_bits, _), plain_s = timed(lambda: st.sample(R, args.batch, 424242))
+    plain_rate = args.batch / plain_s
+    # (1)-(2) training data and training
+    (train_bits, _), data_s = timed(lambda: st.sample(args.train_chib, args.train_samples, 777))
+    h, epochs = 256, 20
+    m = pkg.MADE(n, h, w.made_init(n, h, seed=7))
+    losses, train_s = timed(lambda: m.train(train_bits, 1024, epochs, lr=1e-3,
+                                            orders=w.epoch_orders(args.train_samples, epochs, seed=3)))
+    # (3)-(5) the learned sampler
+    Cn = args.chains
+    T = args.proposals // Cn
+
+    def learned():
+        prop, lg = m.sample(Cn * T, seed=5)
+        lp = 2 * st.amplitude(R, prop)[0]
+        lp0 = 2 * st.amplitude(R, ref_bits[:Cn])[0]
+        state, acc = pkg.mh_independent(lp.reshape(Cn, T), lg.reshape(Cn, T), lp0, m.log_prob(ref_bits[:Cn]), seed=8)
+        return prop, state, acc
+
+    (prop, state, acc), learn_s = timed(learned)
+    state = state.cpu().numpy()
+    propn, starts = prop.cpu().numpy().reshape(Cn, T, n), ref_bits[:Cn].cpu().numpy()
+    held = np.take_along_axis(propn, np.maximum(state, 0)[..., None], 1)
+    chain = np.where(state[..., None] >= 0, held, starts[:, None, :]).reshape(-1, n)
+    rate = float(acc.cpu().numpy().mean() / T)
+    m1_ref, m2_ref = marginals(ref_bits.cpu().numpy())
+    m1, m2 = marginals(chain)
+    m1_prop, m2_prop = marginals(propn.reshape(-1, n))
+    out = {
+        "metric": "learned-proposal samples/s vs plain sampler (independent MH, MADE proposal)",
+        "mode": "learned", "config": {"workload": WORKLOAD, "chi_b": R, "train_chi_b": args.train_chib,
+                                      "train_samples": args.train_samples, "proposals": Cn * T, "chains": Cn,
+                                      "steps": T, "made": f"n={n}, hidden={h}, 4 weight layers, BF16 tcgen05"},
+        "learned_chain_states_per_s": Cn * T / learn_s,
+        "learned_accepted_per_s": float(acc.cpu().numpy().sum()) / learn_s,
+        "acceptance": rate,
+        "plain_samples_per_s": plain_rate,
+        "plain_reference_samples": args.batch,
+        "train": {"data_s": round(data_s, 2), "train_s": round(train_s, 2), "loss_first": float(losses[0]),
+                  "loss_last": float(losses[-1])},
+        "marginals_vs_plain": {
+            "one_site_max_abs": float(np.abs(m1 - m1_ref).max()),
+            "two_site_max_abs": float(np.abs(m2 - m2_ref).max()),
+            "raw_proposals_one_site_max_abs": float(np.abs(m1_prop - m1_ref).max()),
+            "plain_shot_noise_1sigma": float(np.sqrt(0.25 / args.batch)),
+        },
+        "state_build_s": round(build_s, 2),
+    }
+    print(json.dumps(out), flush=True)
+    m.close()
+    st.close()
 
 
 # ---------------------------------------------------------------- reference arm
@@ -425,6 +580,9 @@ def main():
     args = parse()
     if args.gemm_case:
         run_gemm_case(args)
+        return
+    if args.mode == "learned" and args.impl != "reference":
+        run_learned(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -110,9 +110,9 @@ tns_status tns_bp_gauge(tns_state* s, int32_t max_iter, double tol, int32_t* ite
  * Fig. 7d) at boundary rank chi_b (R_x = R_n = chi_b).  Rows of the (oriented)
  * grid are the partitions.  The norm environments are contracted once from the
  * bottom; each sample then absorbs row b into its boundary MPS, compresses it to
- * chi_b (zip-up sweep; truncated SVD by a randomized range finder with one
- * subspace iteration, exact when chi_b + 8 covers the column dimension), draws
- * the row's qubits from their one-site conditionals, and projects.
+ * chi_b (zip-up sweep; truncated SVD of every site matrix by a range finder with
+ * subspace iterations, see tns_set_compression), draws the row's qubits from
+ * their one-site conditionals, and projects.
  *   seed      Philox4x32-10 key: qubit q of sample i uses counter
  *             (i lo, i hi, q, 0); x_q = 1 iff u >= q(0 | prefix)
  *   bits_dev  device uint8 [n_samples][n_sites] (caller-owned)
@@ -157,6 +157,21 @@ tns_status tns_set_precision(tns_state* s, tns_prec prec);
  * smaller ones on FP32 CUDA cores; 0 = all on FP32 CUDA cores.  Shapes the
  * tensor-core kernel does not support fall back to CUDA cores automatically. */
 tns_status tns_set_tensor_cores(tns_state* s, int32_t enable);
+
+/*
+ * tns_set_compression -- settings of the truncated SVD in every zip-up compression
+ * of tns_sample, tns_sample_replay, tns_amplitude and tns_log_norm (the "QR and
+ * truncated SVD" of the boundary-MPS contraction; Methods and Appendix "Sampling
+ * from a Tensor Network State").  The rank-chi_b truncation of each site matrix T
+ * (M x N) is taken from a k = chi_b + oversample column range finder with
+ * power_iters subspace iterations (env_power_iters for the norm environments):
+ * the kept subspace differs from the exact truncated SVD's by a factor
+ * ~(sigma_{k+1} / sigma_chi_b)^(2 q + 1), and k >= N gives the exact truncated SVD.
+ * Defaults: oversample 64, power_iters 3, env_power_iters 6.
+ *   0 <= oversample <= 4096, 0 <= power_iters, env_power_iters <= 64.
+ * Changing them rebuilds the cached norm environments on their next use.
+ */
+tns_status tns_set_compression(tns_state* s, int32_t oversample, int32_t power_iters, int32_t env_power_iters);
 
 /* Query: grid rows/cols after orientation, whether it was transposed, and the
  * current maximum bond dimension. */

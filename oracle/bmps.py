@@ -42,8 +42,12 @@ import numpy as np
 
 from . import philox
 
-OVERSAMPLE = 8
-POWER_ITERS = 1
+# Range-finder settings of the truncated SVD (the library's defaults): k = R + OVERSAMPLE
+# columns and POWER_ITERS subspace iterations in the sampler and amplitude zips,
+# ENV_POWER_ITERS in the norm-environment zips.  Read at call time.
+OVERSAMPLE = 64
+POWER_ITERS = 3
+ENV_POWER_ITERS = 6
 # Shift of the Cholesky orthonormalisation of a range-finder basis, relative to
 # the largest diagonal entry of its Gram matrix: it only regularises
 # rank-deficient bases (orth(Y) is an orthonormal basis of range(Y)).
@@ -93,7 +97,7 @@ def orth(Y: np.ndarray, shift: float) -> np.ndarray:
 
 
 def truncate(T: np.ndarray, R: int, omega, gram_cut: float = ORTH_SHIFT, exact: bool = False,
-             power_iters: int = POWER_ITERS):
+             power_iters: int | None = None, oversample: int | None = None):
     """Rank-R factorisation T ~ K C with K having orthonormal columns (the "QR + truncated SVD").
 
     Randomized range finder with subspace iteration, orthonormalising after every
@@ -102,8 +106,11 @@ def truncate(T: np.ndarray, R: int, omega, gram_cut: float = ORTH_SHIFT, exact: 
     when k = R + p >= N, which makes the step an exact truncated SVD.  Then
     Q = orth(Y), B = Q^H T, B B^H = U_B S^2 U_B^H, K = Q U_B[:, :R], C = K^H T.
     Column phases of K follow ``fix_phase``.  ``gram_cut`` is the orthonormalisation
-    shift.  Returns K (M x Rk), C (Rk x N), Rk = min(R, M, N).
+    shift.  ``power_iters`` / ``oversample`` default to POWER_ITERS / OVERSAMPLE.
+    Returns K (M x Rk), C (Rk x N), Rk = min(R, M, N).
     """
+    power_iters = POWER_ITERS if power_iters is None else power_iters
+    oversample = OVERSAMPLE if oversample is None else oversample
     M, N = T.shape
     Rk = min(R, M, N)
     K = np.zeros((M, Rk), dtype=np.complex128)
@@ -112,7 +119,7 @@ def truncate(T: np.ndarray, R: int, omega, gram_cut: float = ORTH_SHIFT, exact: 
         n = min(Rk, s.size)
         K[:, :n] = fix_phase(U[:, :n])
         return K, K.conj().T @ T
-    kk = min(R + OVERSAMPLE, M, N)
+    kk = min(R + oversample, M, N)
     if kk == N:
         Y = T
     else:
@@ -128,7 +135,7 @@ def truncate(T: np.ndarray, R: int, omega, gram_cut: float = ORTH_SHIFT, exact: 
     return K, K.conj().T @ T
 
 
-def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT):
+def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT, power_iters=None):
     """Zip-up MPS-MPO compression to rank R along the given (logical) site order.
 
     T_j[(k, y, xp), (a', r)] = sum C_{j-1}[k, a, l] m_j[a, xc, xp, a'] w_j[l, xc, y, r];
@@ -153,18 +160,19 @@ def zip_compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT
             out.append((Tm / nrm if nrm > 0 else Tm).reshape(k, y, xp, 1))
             break
         omega = lambda n, kk, _j=j: philox.test_matrix(seed, stage, row, _j, n, kk)
-        K, Cn = truncate(Tm, R, omega, gram_cut=gram_cut, exact=exact)
+        K, Cn = truncate(Tm, R, omega, gram_cut=gram_cut, exact=exact, power_iters=power_iters)
         out.append(K.reshape(k, y, xp, K.shape[1]))
         C = Cn.reshape(Cn.shape[0], ap, r)
     return out, log_scale
 
 
-def compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT, fit_sweeps=0):
+def compress(mps, mpo, R, seed, stage, row, exact=False, gram_cut=ORTH_SHIFT, fit_sweeps=0, power_iters=None):
     """The zip-up compression, followed by ``fit_sweeps`` sweeps of one-site
     variational fitting when fit_sweeps > 0 (the paper's compressor)."""
     if fit_sweeps > 0:
-        return fit_compress(mps, mpo, R, seed, stage, row, sweeps=fit_sweeps, exact=exact, gram_cut=gram_cut)
-    return zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut)
+        return fit_compress(mps, mpo, R, seed, stage, row, sweeps=fit_sweeps, exact=exact, gram_cut=gram_cut,
+                            power_iters=power_iters)
+    return zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut, power_iters=power_iters)
 
 
 def mirror_mps(mps):
@@ -211,7 +219,7 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False, fit_sweep
             s, u, l, d, r = t.shape
             mpo.append(np.transpose(t, (2, 3, 0, 1, 4)).reshape(l, d, s * u, r))
         Z, ls1 = compress(m, mpo, R, seed, philox.STAGE_ENV_KET, b, exact=exact, gram_cut=gram_cut,
-                          fit_sweeps=fit_sweeps)
+                          fit_sweeps=fit_sweeps, power_iters=ENV_POWER_ITERS)
         # Z_j: k, (s,u), dbar, k' -> bra input: Xc = (s, dbar), Xp = u
         mz, mpo2 = [], []
         for zj, t in zip(Z, row):
@@ -222,7 +230,7 @@ def norm_envs(tns, R, seed=ENV_SEED, gram_cut=ORTH_SHIFT, exact=False, fit_sweep
             mpo2.append(np.transpose(t.conj(), (2, 0, 3, 1, 4)).reshape(l, s * d, u, r))
         mz, mpo2 = mirror_mps(mz), list(reversed([np.transpose(w, (3, 1, 2, 0)) for w in mpo2]))
         Eb, ls2 = compress(mz, mpo2, R, seed, philox.STAGE_ENV_BRA, b, exact=exact, gram_cut=gram_cut,
-                           fit_sweeps=fit_sweeps)
+                           fit_sweeps=fit_sweeps, power_iters=ENV_POWER_ITERS)
         Eb = mirror_mps(Eb)                                          # back to column order
         E[b] = [np.transpose(x, (0, 2, 1, 3)) for x in Eb]           # e, u(ket), ubar, e'
         log_norm += ls1 + ls2
@@ -417,7 +425,8 @@ def _product_site(m, w):
     return np.einsum("acpA,lcyr->alypAr", m, w)
 
 
-def fit_compress(mps, mpo, R, seed, stage, row, sweeps=2, exact=False, gram_cut=ORTH_SHIFT, history=None):
+def fit_compress(mps, mpo, R, seed, stage, row, sweeps=2, exact=False, gram_cut=ORTH_SHIFT, history=None,
+                 power_iters=None):
     """MPS-MPO compression to rank R by one-site variational fitting (Methods and
     Appendix "Sampling...": maximise the overlap of the output MPS with the exact
     MPS-MPO product by sweeping through the output's sites and replacing each with
@@ -433,7 +442,7 @@ def fit_compress(mps, mpo, R, seed, stage, row, sweeps=2, exact=False, gram_cut=
     |<Y|P>| / |Y| after every local update.
     """
     W = len(mps)
-    Y, _ = zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut)
+    Y, _ = zip_compress(mps, mpo, R, seed, stage, row, exact=exact, gram_cut=gram_cut, power_iters=power_iters)
     P = [_product_site(m, w) for m, w in zip(mps, mpo)]
     one = np.ones((1, 1, 1), dtype=np.complex128)
 

@@ -136,6 +136,11 @@ class TNSState:
     PROFILE_CLASSES = ("env_gemm", "sweep_gemm", "zip_gemm", "eigh", "marginal", "tc_prep", "tc_prep_sweep",
                        "tc_prep_zip", "zip_simt", "sweep_simt")
 
+    def set_compression(self, oversample: int, power_iters: int, env_power_iters: int):
+        """Range-finder settings of the truncated SVDs (see tns_set_compression)."""
+        check(self.lib.tns_set_compression(self._h, int(oversample), int(power_iters), int(env_power_iters)),
+              "tns_set_compression")
+
     def set_tensor_cores(self, enable: bool):
         check(self.lib.tns_set_tensor_cores(self._h, 1 if enable else 0), "tns_set_tensor_cores")
 

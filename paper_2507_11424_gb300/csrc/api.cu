@@ -322,6 +322,19 @@ extern "C" tns_status tns_set_tensor_cores(tns_state* s, int32_t enable) {
   return TNS_OK;
 }
 
+extern "C" tns_status tns_set_compression(tns_state* s, int32_t oversample, int32_t power_iters,
+                                          int32_t env_power_iters) {
+  if (!s || oversample < 0 || oversample > 4096 || power_iters < 0 || power_iters > 64 || env_power_iters < 0 ||
+      env_power_iters > 64) {
+    set_error("invalid argument to tns_set_compression");
+    return TNS_ERR_ARG;
+  }
+  s->rf_p = oversample;
+  s->rf_q = power_iters;
+  s->rf_q_env = env_power_iters;
+  return TNS_OK;
+}
+
 extern "C" tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int32_t* transposed, int32_t* chi_now) {
   if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
   int chi = 1;

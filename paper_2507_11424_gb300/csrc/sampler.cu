@@ -150,27 +150,35 @@ template <typename C> __global__ void normalize_kernel(C* F, long long n) {
   for (long long i = threadIdx.x; i < n; i += blockDim.x) F[b * n + i] = from_cd<C>(cscale(to_cd(F[b * n + i]), inv));
 }
 
-// One qubit of one sample per block: rho(s) = Re sum_e G[s][e] F[e]; q0 = rho0 / sum;
-// draw x = [u >= q0] (or read the forced bit); log q += log q(x); L_next = G[x] / sum;
-// m_next = K'[:, x, :, :].
+// Conditional marginals of one qubit for every sample of the chunk, in two
+// kernels with MARG_SPLIT blocks per sample (enough blocks to fill the GPU at any
+// chunk size):
+//   marginal_partial_kernel: block (k, i) sums its slice of
+//     rho_s = Re sum_e G[i][s][e] F[i][e]  (s = 0, 1) into part[i][k][s];
+//   marginal_draw_kernel: every block of sample i adds the MARG_SPLIT partials in
+//     index order (the same total in every block), forms q0 = rho0 / (rho0 + rho1)
+//     (negative rho clamped to 0), takes x from the Philox uniform u (x = [u >= q0])
+//     or the forced bit, and copies its slice of L_next = G[x] / (rho0 + rho1) and
+//     of m_next = K'[:, x, :, :]; block 0 writes the bit, q0 and log q(x).
+constexpr int MARG_SPLIT = 8;
 template <typename C>
-__global__ void marginal_kernel(const C* G, int P, long long nel, const C* F, long long fstride, const C* Kp,
-                                long long kstride, int ka, int Dd, int kb, C* Lnext, C* mnext, uint8_t* bits,
-                                const uint8_t* forced, int n_sites, int qubit, double* logq, double* cond,
-                                uint64_t seed, long long sample0) {
-  const long long sidx = blockIdx.x;
+__global__ void __launch_bounds__(256)
+marginal_partial_kernel(const C* __restrict__ G, int P, long long nel, const C* __restrict__ F, long long fstride,
+                        double* __restrict__ part) {
+  const long long sidx = blockIdx.y;
+  const int k = blockIdx.x;
+  const long long per = (nel + MARG_SPLIT - 1) / MARG_SPLIT;
+  const long long e0 = k * per, e1 = min(nel, e0 + per);
   const C* g = G + sidx * P * nel;
   const C* f = F + sidx * fstride;
   __shared__ double r0[256], r1[256];
-  __shared__ int xs;
-  __shared__ double invs;
   double a0 = 0.0, a1 = 0.0;
-  for (long long e = threadIdx.x; e < nel; e += blockDim.x) {
-    cd fv = to_cd(f[e]);
-    cd g0 = to_cd(g[e]);
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const cd fv = to_cd(f[e]);
+    const cd g0 = to_cd(g[e]);
     a0 += g0.x * fv.x - g0.y * fv.y;
     if (P > 1) {
-      cd g1 = to_cd(g[nel + e]);
+      const cd g1 = to_cd(g[nel + e]);
       a1 += g1.x * fv.x - g1.y * fv.y;
     }
   }
@@ -182,24 +190,47 @@ __global__ void marginal_kernel(const C* G, int P, long long nel, const C* F, lo
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double p0 = fmax(r0[0], 0.0), p1 = (P > 1) ? fmax(r1[0], 0.0) : 0.0;
-    double tot = p0 + p1;
+    part[(sidx * MARG_SPLIT + k) * 2] = r0[0];
+    part[(sidx * MARG_SPLIT + k) * 2 + 1] = r1[0];
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+marginal_draw_kernel(const double* __restrict__ part, const C* __restrict__ G, int P, long long nel,
+                     const C* __restrict__ Kp, long long kstride, int ka, int Dd, int kb, C* __restrict__ Lnext,
+                     C* __restrict__ mnext, uint8_t* bits, const uint8_t* forced, int n_sites, int qubit, double* logq,
+                     double* cond, uint64_t seed, long long sample0) {
+  const long long sidx = blockIdx.y;
+  const int k = blockIdx.x;
+  __shared__ int xs;
+  __shared__ double invs;
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < MARG_SPLIT; ++i) {
+      s0 += part[(sidx * MARG_SPLIT + i) * 2];
+      s1 += part[(sidx * MARG_SPLIT + i) * 2 + 1];
+    }
+    const double p0 = fmax(s0, 0.0), p1 = (P > 1) ? fmax(s1, 0.0) : 0.0;
+    const double tot = p0 + p1;
     int x = 0;
     if (P > 1) {
-      double q0 = tot > 0.0 ? p0 / tot : 0.5;
-      long long gs = sample0 + sidx;
+      const double q0 = tot > 0.0 ? p0 / tot : 0.5;
+      const long long gs = sample0 + sidx;
       if (forced) {
         x = forced[gs * n_sites + qubit] ? 1 : 0;
       } else {
         Philox4 w = philox4x32_10((uint32_t)((uint64_t)gs & 0xffffffffu), (uint32_t)((uint64_t)gs >> 32),
                                   (uint32_t)qubit, 0u, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-        double u = u53(w.v[0], w.v[1]);
+        const double u = u53(w.v[0], w.v[1]);
         x = (u >= q0) ? 1 : 0;
-        bits[gs * n_sites + qubit] = (uint8_t)x;
       }
-      double qx = x ? 1.0 - q0 : q0;
-      logq[gs] += qx > 0.0 ? log(qx) : -INFINITY;
-      if (cond) cond[gs * n_sites + qubit] = q0;
+      if (k == 0) {
+        if (!forced) bits[gs * n_sites + qubit] = (uint8_t)x;
+        const double qx = x ? 1.0 - q0 : q0;
+        logq[gs] += qx > 0.0 ? log(qx) : -INFINITY;
+        if (cond) cond[gs * n_sites + qubit] = q0;
+      }
     }
     xs = x;
     invs = tot > 0.0 ? 1.0 / tot : 1.0;
@@ -207,12 +238,17 @@ __global__ void marginal_kernel(const C* G, int P, long long nel, const C* F, lo
   __syncthreads();
   const int x = xs;
   const double inv = invs;
-  for (long long e = threadIdx.x; e < nel; e += blockDim.x)
-    Lnext[sidx * nel + e] = from_cd<C>(cscale(to_cd(g[(long long)x * nel + e]), inv));
+  const long long per = (nel + MARG_SPLIT - 1) / MARG_SPLIT;
+  const long long e1 = min(nel, (k + 1) * per);
+  const C* g = G + (sidx * P + x) * nel;
+  for (long long e = k * per + threadIdx.x; e < e1; e += blockDim.x)
+    Lnext[sidx * nel + e] = from_cd<C>(cscale(to_cd(g[e]), inv));
   const C* kp = Kp + sidx * kstride;
-  long long nm = (long long)ka * Dd * kb;
-  for (long long e = threadIdx.x; e < nm; e += blockDim.x) {
-    long long a = e / ((long long)Dd * kb), rem = e % ((long long)Dd * kb);
+  const long long nm = (long long)ka * Dd * kb;
+  const long long mper = (nm + MARG_SPLIT - 1) / MARG_SPLIT;
+  const long long m1 = min(nm, (k + 1) * mper);
+  for (long long e = k * mper + threadIdx.x; e < m1; e += blockDim.x) {
+    const long long a = e / ((long long)Dd * kb), rem = e % ((long long)Dd * kb);
     mnext[sidx * nm + e] = kp[((a * P + x) * Dd) * kb + rem];
   }
 }
@@ -401,7 +437,8 @@ struct Ctx {
   size_t esz;
   uint64_t seed;
   int R;
-
+  int p = 8;      // range-finder oversampling: k = R + p columns
+  int q = 1;      // subspace iterations (T T^H applications)
 };
 
 template <typename F> static void dispatch(bool f64, F&& f) {
@@ -508,7 +545,7 @@ static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
 // FP32 (Gram and products in FP32, the kk x kk Cholesky in FP64): a first pass
 // with shift 1e-5 gives a well-conditioned basis of the same range, two more
 // passes restore orthonormality to FP32 accuracy without damping any direction.
-static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void* Qout) {
+static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void* Qout, bool span_only = false) {
   tns_state* s = cx.s;
   void *G, *Wm;
   TNS_TRY(wsget(s, "z_G", sizeof(cd) * S * kk * kk, &G));
@@ -526,6 +563,9 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
     return TNS_OK;
   };
   if (cx.f64) return pass(Y, Qout, ORTH_SHIFT_FP64);
+  // between subspace iterations only the span matters: one pass gives a basis of the
+  // same range that is orthonormal to ~eps * cond(Y)^2
+  if (span_only) return pass(Y, Qout, ORTH_SHIFT_CQR_FIRST);
   void* tmp;
   TNS_TRY(wsget(s, "z_Q2", cx.esz * S * M * kk, &tmp));
   TNS_TRY(pass(Y, Qout, ORTH_SHIFT_CQR_FIRST));
@@ -534,18 +574,21 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
 }
 
 // Rank-R factorisation T = K C of each batch entry (T: S x M x N): randomized
-// range finder with one subspace iteration, orthonormalising after every
-// application (Halko, Martinsson, Tropp 2011, Alg. 4.4):
-//   Y0 = T Omega, Q0 = orth(Y0), Z = orth(T^H Q0), Y = T Z, Q = orth(Y),
+// range finder with q subspace iterations (Halko, Martinsson, Tropp 2011, Alg. 4.4),
+// orthonormalising after every application:
+//   Y = T Omega (k = R + p columns); q times { Z = orth(T^H orth(Y)), Y = T Z };
+//   Q = orth(Y),
 // then the truncated SVD of B = Q^H T from the eigendecomposition of B B^H (FP64
 // path: FP64; mixed path: FP32, the precision B carries):
 //   K = Q U_B[:, :R] (column phases fixed), C = K^H T (returned conjugate-transposed).
-// The products that contract over M read T^H from one transposed copy.
-// With k = R + 8 >= N the test matrix is the identity and Y = T.
+// The error of the kept subspace shrinks like (sigma_{k+1} / sigma_R)^(2q+1), so
+// flat spectra at the cut need k well above R and a few iterations.  The products
+// that contract over M read T^H from one transposed copy.  With k >= N the test
+// matrix is the identity and Y = T: the step is an exact truncated SVD.
 static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long N, int stage, int row, int site,
                            void* Kout, void* Cout, int* Rk_out) {
   tns_state* s = cx.s;
-  const int kk = (int)std::min<long long>(std::min<long long>(cx.R + 8, M), N);
+  const int kk = (int)std::min<long long>(std::min<long long>(cx.R + cx.p, M), N);
   const int Rk = (int)std::min<long long>(std::min<long long>(cx.R, M), N);
   *Rk_out = Rk;
   void *Y, *Q, *Z, *B, *UBt, *om;
@@ -554,7 +597,7 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
   TNS_TRY(wsget(s, "z_Z", cx.esz * S * N * kk, &Z));
   TNS_TRY(wsget(s, "z_B", cx.esz * S * N * kk, &B));
   TNS_TRY(wsget(s, "z_UBt", cx.esz * S * kk * kk, &UBt));
-  // Th = T^H (per batch entry), read in place by the three products that contract over M
+  // Th = T^H (per batch entry), read in place by the products that contract over M
   void* Th;
   TNS_TRY(wsget(s, "z_Th", cx.esz * S * M * N, &Th));
   dispatch(cx.f64, [&](auto* tp) {
@@ -575,12 +618,14 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     s->launches++;
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}),
                            cx.gp));
-    TNS_TRY(orth(cx, Y, S, M, kk, Q));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Q, "Sme", {S, M, kk}),
-                           view(Z, "Sne", {S, N, kk}), cx.gp));
-    TNS_TRY(orth(cx, Z, S, N, kk, B));
-    TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(B, "Sne", {S, N, kk}),
-                           view(Y, "Sme", {S, M, kk}), cx.gp));
+    for (int it = 0; it < cx.q; ++it) {
+      TNS_TRY(orth(cx, Y, S, M, kk, Q, true));
+      TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Q, "Sme", {S, M, kk}),
+                             view(Z, "Sne", {S, N, kk}), cx.gp));
+      TNS_TRY(orth(cx, Z, S, N, kk, B, true));
+      TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(B, "Sne", {S, N, kk}),
+                             view(Y, "Sme", {S, M, kk}), cx.gp));
+    }
   }
   TNS_TRY(orth(cx, Ymat, S, M, kk, Q));
   // Bt = T^H Q = conj(B)^T with B = Q^H T; read T^H in place from Th
@@ -732,9 +777,11 @@ static tns_status build_envs(Ctx& cx_in) {
   Ctx cx = cx_in;
   cx.seed = 0;
   tns_state* s = cx.s;
+  cx.q = s->rf_q_env;
   EnvCache& ec = s->env;
   const int prec = cx.f64 ? 0 : 1;
-  if (ec.valid && ec.chi_b == cx.R && ec.prec == prec && ec.version == s->version) return TNS_OK;
+  if (ec.valid && ec.chi_b == cx.R && ec.prec == prec && ec.version == s->version && ec.p == cx.p && ec.q == cx.q)
+    return TNS_OK;
   for (auto& E : ec.E) free_mps(E);
   ec.E.assign(s->H + 1, StoredMPS());
   ec.valid = false;
@@ -824,6 +871,8 @@ static tns_status build_envs(Ctx& cx_in) {
   ec.chi_b = cx.R;
   ec.prec = prec;
   ec.version = s->version;
+  ec.p = cx.p;
+  ec.q = cx.q;
   return TNS_OK;
 }
 
@@ -835,6 +884,8 @@ static tns_status make_ctx(tns_state* s, int chi_b, uint64_t seed, Ctx& cx) {
   cx.esz = cx.f64 ? sizeof(cd) : sizeof(cf);
   cx.seed = seed;
   cx.R = chi_b;
+  cx.p = s->rf_p;
+  cx.q = s->rf_q;
   return ensure_work_cells(s, cx.f64);
 }
 
@@ -933,6 +984,8 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   TNS_TRY(wsget(s, "s_G", cx.esz * chunk * 2 * F_cap, &Gb));
   TNS_TRY(wsget(s, "s_bigA", cx.esz * chunk * big_cap, &bigA));
   TNS_TRY(wsget(s, "s_bigB", cx.esz * chunk * big_cap, &bigB));
+  double* mpart;
+  TNS_TRY(wsget(s, "s_mpart", sizeof(double) * 2 * MARG_SPLIT * chunk, (void**)&mpart));
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
     fill_kernel<C><<<nblk(chunk), 256, 0, cx.st>>>((C*)ones, chunk, 1.0);
@@ -1037,10 +1090,14 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         cudaEvent_t mev = s->prof.begin(cx.st);
         dispatch(cx.f64, [&](auto* tp) {
           using C = std::remove_pointer_t<decltype(tp)>;
-          marginal_kernel<C><<<(unsigned)S, 256, 0, cx.st>>>(
-              (const C*)Gb, (int)P, nel, (const C*)Fs[j + 1], fst, (const C*)Kp.site[j], kst, (int)ka, (int)Dd,
-              (int)kb, (C*)Ln, (C*)mnext.site[j], bits, forced, s->n, q < 0 ? 0 : q, logq, cond, cx.seed, s0);
+          const dim3 grid(MARG_SPLIT, (unsigned)S);
+          marginal_partial_kernel<C><<<grid, 256, 0, cx.st>>>((const C*)Gb, (int)P, nel, (const C*)Fs[j + 1], fst,
+                                                              mpart);
+          marginal_draw_kernel<C><<<grid, 256, 0, cx.st>>>(
+              mpart, (const C*)Gb, (int)P, nel, (const C*)Kp.site[j], kst, (int)ka, (int)Dd, (int)kb, (C*)Ln,
+              (C*)mnext.site[j], bits, forced, s->n, q < 0 ? 0 : q, logq, cond, cx.seed, s0);
         });
+        s->launches++;
         s->prof.end(PC_MARG, mev, 0.0, cx.st);
         s->launches++;
         mnext.phys[j] = {Dd};

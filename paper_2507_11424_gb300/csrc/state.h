@@ -63,6 +63,7 @@ struct EnvCache {
   int chi_b = 0;
   int prec = -1;
   long long version = -1;
+  int p = -1, q = -1;                   // range-finder settings the environments were built with
   std::vector<StoredMPS> E;             // E[b], b = 1..H (index b); each stored right-to-left
   double log_norm = 0.0;
 };
@@ -92,6 +93,9 @@ struct tns_state {
   std::vector<void*> work_cells;        // working-precision copies of the cell tensors
   int work_prec = -1;
   bool tensor_cores = true;             // mixed path: environment GEMMs on tcgen05
+  int rf_p = 64;                        // range-finder oversampling (k = chi_b + rf_p columns)
+  int rf_q = 3;                         // subspace iterations of the sampler and amplitude zips
+  int rf_q_env = 6;                     // subspace iterations of the norm-environment zips
   long long work_version = -1;
 
   int cidx(int r, int c) const { return r * W + c; }

@@ -2,6 +2,7 @@
 #pragma once
 #include "common.cuh"
 #include <string.h>
+#include <cuda.h>
 
 namespace tns {
 
@@ -63,6 +64,10 @@ __host__ __device__ inline float tf32_rn(float x) {
 inline int tc_tile_n(long long n_complex) { return 2 * n_complex <= 128 ? 128 : 256; }
 
 bool tc_available();
+// 2-D TMA descriptor (128B swizzle, zero fill out of bounds) over a row-major
+// [rows][cols] FP32 or BF16 array with a row pitch of ld_bytes (multiple of 16).
+bool tma_map_2d(CUtensorMap* map, bool bf16, const void* ptr, long long rows, long long cols, long long ld_bytes,
+                int box_cols, int box_rows);
 // cudaErrorNotSupported when the shape or alignment does not fit the kernel.
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st);
 // Per-device error flag shared by every tensor-core launch (lazily allocated).

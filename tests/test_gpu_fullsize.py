@@ -1,56 +1,87 @@
-"""Full-size parity on the benchmark workload (GPU, several minutes).
+"""Full-size parity on the benchmark workload against the exact-SVD oracle (GPU).
 
 10x10 square lattice, domain-wall Heisenberg quench, 7 layers, dt = 0.2,
-chi = 16, boundary rank chi_b = 64: the state is built by the library, written
-as a fixture, and the CPU oracle replays the conditionals q(x_v = 0 | prefix)
-along bitstrings the library drew, one sample per precision path.
+chi = 16, boundary rank chi_b = 64.  The state is built by the CPU oracle (the
+same function that wrote the stored reference, ``build_state`` in
+tests/golden/make_sq10x10_exact.py) and loaded into the library from a TNSF
+file.  The stored reference holds, for 16 samples drawn by the oracle with every
+truncation an exact truncated SVD (norm environments included), the bits, every
+conditional q(x_v = 0 | prefix) and log q.  The library replays those bitstrings
+in both precision paths with its default compression settings (range finder with
+oversampling and subspace iterations, see tns_set_compression), and draws its own
+samples from the same seed.
+
+Bar (the metric's marginal-error bound): every conditional within 1e-3 of the
+exact oracle's, in both paths.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
-import workloads as w
-from oracle import bmps, fixture
-
 pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden", "sq10x10_chib64_exact.npz")
+TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
 def state(tmp_path_factory):
     import paper_2507_11424_gb300 as pkg
     from paper_2507_11424_gb300 import build
+    from oracle import fixture
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    from make_sq10x10_exact import build_state
     build.build()
-    cfg = w.CONFIGS["sq10x10"]
-    lat = w.make_lattice(cfg["lattice"])
-    bits = w.domain_wall_bits(lat)
-    st = pkg.TNSState(lat.grid_rc, lat.edges, bits, chi_max=cfg["chi"], prec="mixed")
-    for g in w.heisenberg_circuit(lat, cfg["layers"], cfg["dt"]):
-        st.apply_gate_layer(g, chi=cfg["chi"])
-        st.bp_gauge(300, 1e-10)
+    gold = dict(np.load(GOLD))
+    t, cfg, _ = build_state()
+    # the rebuilt oracle state is the one the reference was computed on
+    assert abs(t.log_fidelity - float(gold["log_fidelity"])) < 1e-9
     path = str(tmp_path_factory.mktemp("cfg2") / "cfg2.tnsf")
-    st.save(path)
-    return st, fixture.load(path), cfg, bits
+    fixture.save(t, path)
+    st = pkg.TNSState.load_file(path)
+    st.n = t.n
+    yield st, gold, cfg
+    st.close()
 
 
-# Tolerances.  FP64: rounding only (1e-8).  Mixed (complex64 storage, TF32x3 tensor-core
-# contractions, FP32 Gram / Cholesky / Jacobi in the truncation): at chi_b = 64 this
-# state is truncated hard, and replaying the same bitstrings in FP64 with a different
-# range-finder test matrix already moves single conditionals by ~2.6e-2 -- the
-# method's own spread between equally valid runs.  FP32-level rounding moves them by
-# up to ~6e-3.  The mixed bar is 1e-2 on the largest conditional (below that spread)
-# and 1e-3 on the mean over all conditionals of the sample.
-@pytest.mark.parametrize("prec,shift,tol", [("mixed", bmps.ORTH_SHIFT, 1e-2), ("fp64", bmps.ORTH_SHIFT, 1e-8)])
-def test_fullsize_conditionals_match_oracle(state, prec, shift, tol):
-    st, t, cfg, bits = state
-    R = cfg["chi_b"]
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_fullsize_replay_matches_exact_oracle(state, prec):
+    import torch
+    st, gold, cfg = state
+    R = int(gold["chi_b"])
     st.set_precision(prec)
-    n = 8 if prec == "mixed" else 1
-    xs, logq, cond = st.sample(R, n, seed=20250711, cond=True)
-    xs, logq, cond = xs.cpu().numpy(), logq.cpu().numpy(), cond.cpu().numpy()
+    bits = torch.tensor(gold["bits"], dtype=torch.uint8, device="cuda")
+    logq, cond = st.sample_replay(R, bits)
+    cond, logq = cond.cpu().numpy(), logq.cpu().numpy()
+    err = np.abs(cond - gold["q0"])
+    assert bits.shape[0] >= 16
     assert np.isfinite(logq).all()
-    assert (xs.sum(axis=1) == bits.sum()).mean() >= 0.5          # U(1) sector mostly kept at chi_b = 64
-    E, _ = bmps.norm_envs(t, R, gram_cut=shift)
-    _, lq_o, q0_o = bmps.sample(t, R, 0, 20250711, forced=xs[:1], env=E, gram_cut=shift)
-    err = np.abs(cond[:1] - q0_o).max()
-    assert err < tol, f"max |q_gpu - q_oracle| = {err:.3e}"
-    assert np.abs(cond[:1] - q0_o).mean() < tol / 10
-    assert abs(logq[0] - lq_o[0]) < 50 * tol
+    assert err.max() < TOL, f"{prec}: max |q - q_exact| = {err.max():.3e} (mean {err.mean():.3e})"
+    # log q is a sum of 100 log conditionals, each within TOL of the oracle's
+    assert np.abs(logq - gold["logq"]).max() < 100 * TOL / 0.05
+
+
+def test_fullsize_draws_follow_exact_oracle(state):
+    """Same seed, same sample indices: the library's draws equal the oracle's wherever the
+    uniform is not within the tolerance of the conditional it is compared with."""
+    from oracle import philox
+    st, gold, cfg = state
+    R = int(gold["chi_b"])
+    st.set_precision("mixed")
+    n = gold["bits"].shape[0]
+    xs, logq, cond = st.sample(R, n, seed=int(gold["seed"]), cond=True)
+    xs, cond = xs.cpu().numpy(), cond.cpu().numpy()
+    same = 0
+    for i in range(n):
+        if np.array_equal(xs[i], gold["bits"][i]):
+            same += 1
+            continue
+        # the first qubit where they part must be a near tie of u and q0
+        u = philox.draw_uniforms(int(gold["seed"]), i, np.arange(xs.shape[1]))
+        diff = np.flatnonzero(xs[i] != gold["bits"][i])
+        gap = np.abs(u[diff] - gold["q0"][i, diff])
+        assert gap.min() < TOL, f"sample {i}: draws part at a qubit with |u - q0| = {gap.min():.3e}"
+    assert same >= n - 2
