@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=128)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compression", default=None, metavar="P,Q,QENV",
+                    help="range-finder oversampling, subspace iterations, environment iterations (library defaults)")
     ap.add_argument("--plain-samples", type=int, default=8,
                     help="samples the plain FP64 sampler replays for its rate and the marginal error (0 = skip)")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
@@ -237,18 +239,19 @@ def plain_sampler(st, R, args, seed0):
     """
     import torch
     n = args.plain_samples
-    xs, _, cond_m = st.sample(R, n, seed0 + 300, cond=True)
+    seed = seed0 + 300              # the same seed keys the same range-finder test matrices in both paths
+    xs, _, cond_m = st.sample(R, n, seed, cond=True)
     st.set_precision("fp64")
     try:
         t0 = time.time()
         st.log_norm(R)                            # FP64 norm environments (setup, as for the mixed path)
         env_s = time.time() - t0
-        st.sample_replay(R, xs[:1])               # warm-up
+        st.sample_replay(R, xs[:1], seed)         # warm-up
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        _, cond_p = st.sample_replay(R, xs)
+        _, cond_p = st.sample_replay(R, xs, seed)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -285,6 +288,8 @@ def run_gpu(args):
             st.save(args.state_cache)
     torch.cuda.synchronize()
     build_s = time.time() - t0
+    if args.compression:
+        st.set_compression(*(int(x) for x in args.compression.split(",")))
     t0 = time.time()
     log_norm = st.log_norm(R)
     torch.cuda.synchronize()

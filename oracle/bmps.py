@@ -13,14 +13,18 @@ following the paper's Appendix "Sampling from a Tensor Network State" (Fig. 7):
   projected row becomes m_{b+1};
 * q(x) is the product of the conditionals.
 
-The MPS-MPO compression is a zip-up sweep whose per-site truncated SVD is taken
-by the randomized range finder (Halko, Martinsson, Tropp 2011, Alg. 4.4: a
-shared Philox test matrix, one subspace iteration with an orthonormalisation
-after every application, then an SVD of the projected matrix): the rank-R
-truncation that the library computes.  When R + oversampling covers the full
-column dimension the test matrix is the identity and the step is an exact
-truncated SVD.  ``zip_compress(exact=True)`` takes the plain SVD instead and is
-used to pin the range finder.  ``fit_sweeps > 0`` follows the zip with the
+The MPS-MPO compression is a zip-up sweep whose per-site truncated SVD (the
+"QR and truncated SVD" of the method) has two forms here.  ``exact=True`` is the
+plain definition: LAPACK's SVD of the site matrix, keep the top R singular
+vectors.  The default follows the library's computation of the same truncation,
+a randomized range finder (Halko, Martinsson, Tropp 2011, Alg. 4.4: a shared
+Philox test matrix with R + OVERSAMPLE columns, POWER_ITERS subspace iterations
+with an orthonormalisation after every application, then an SVD of the
+projected matrix), whose kept subspace converges to the exact one like
+(sigma_{k+1} / sigma_R)^(2q+1); when R + oversampling covers the full column
+dimension the test matrix is the identity and the step is exact.  Tests compare
+the library with both: the randomized form pins the implementation to rounding,
+the exact form bounds how far the method's result is from the definition.  ``fit_sweeps > 0`` follows the zip with the
 paper's one-site variational fitting (``fit_compress``; Methods and Fig. 7c),
 which only raises the overlap with the exact MPS-MPO product.
 
@@ -45,7 +49,7 @@ from . import philox
 # Range-finder settings of the truncated SVD (the library's defaults): k = R + OVERSAMPLE
 # columns and POWER_ITERS subspace iterations in the sampler and amplitude zips,
 # ENV_POWER_ITERS in the norm-environment zips.  Read at call time.
-OVERSAMPLE = 64
+OVERSAMPLE = 48
 POWER_ITERS = 3
 ENV_POWER_ITERS = 6
 # Shift of the Cholesky orthonormalisation of a range-finder basis, relative to
@@ -364,15 +368,38 @@ class _Flipped:
                   for b in range(tns.H)]
 
 
-def direct_marginals(tns, R, gram_cut=ORTH_SHIFT, exact=False):
+def _grow_left(L, U, t, o, D):
+    """L'[e', r, rb, f'] = sum L[e, l, lb, f] U[e, u, ub, e'] t[s, u, l, d, r] o[s, s']
+    conj t[s', ub, lb, db, rb] D[f, d, db, f']: one site of a row of the norm network
+    between its top (U) and bottom (D) environments, absorbed from the left."""
+    X = np.tensordot(L, U, axes=([0], [0]))                    # l, lb, f, u, ub, e'
+    X = np.tensordot(X, t, axes=([0, 3], [2, 1]))              # lb, f, ub, e', s, d, r
+    tb = np.tensordot(o, t.conj(), axes=([1], [0]))            # s, ub, lb, db, rb
+    X = np.tensordot(X, tb, axes=([0, 2, 4], [2, 1, 0]))       # f, e', d, r, db, rb
+    return np.tensordot(X, D, axes=([0, 2, 4], [0, 1, 2]))     # e', r, rb, f'
+
+
+def _grow_right(Rt, U, t, o, D):
+    """The same site absorbed from the right: R'[e, l, lb, f] from R[e', r, rb, f']."""
+    X = np.tensordot(U, Rt, axes=([3], [0]))                   # e, u, ub, r, rb, f'
+    X = np.tensordot(X, t, axes=([1, 3], [1, 4]))              # e, ub, rb, f', s, l, d
+    tb = np.tensordot(o, t.conj(), axes=([1], [0]))            # s, ub, lb, db, rb
+    X = np.tensordot(X, tb, axes=([1, 2, 4], [1, 4, 0]))       # e, f', l, d, lb, db
+    return np.tensordot(X, D, axes=([1, 3, 5], [3, 1, 2]))     # e, l, lb, f
+
+
+def direct_marginals(tns, R, gram_cut=ORTH_SHIFT, exact=False, pairs=True):
     """Sample-free marginals <n_q> = <psi|P1_q|psi>/<psi|psi> for every qubit and
     <n_q n_q'> for every pair in the same grid row (NaN for pairs in different
-    rows), by boundary-MPS contraction of the norm network <psi|psi>.
+    rows, and for all pairs when ``pairs`` is False), by boundary-MPS contraction of
+    the norm network <psi|psi>.
 
     Row b is contracted exactly between its top environment (rows 0..b-1, the
     bottom environments of the upside-down TNS) and its bottom environment E[b+1]
-    (rows b+1..H-1), both compressed to rank R as in norm_envs.  Exact when R
-    covers the environments' ranks.  Returns (one [n], two [n, n]).
+    (rows b+1..H-1), both compressed to rank R as in norm_envs, one site at a time
+    from the left and from the right, with the projector P1 = |1><1| inserted on
+    the physical legs of the marginal's qubits.  Exact when R covers the
+    environments' ranks.  Returns (one [n], two [n, n]).
     """
     H, W = tns.H, tns.W
     E, _ = norm_envs(tns, R, gram_cut=gram_cut, exact=exact)
@@ -380,42 +407,36 @@ def direct_marginals(tns, R, gram_cut=ORTH_SHIFT, exact=False):
     n = int((tns.cell_qubit >= 0).sum())
     one = np.full(n, np.nan)
     two = np.full((n, n), np.nan)
-    P = [np.eye(2, dtype=np.complex128), np.diag([0.0, 1.0]).astype(np.complex128)]
+    P1 = np.diag([0.0, 1.0]).astype(np.complex128)
     for b in range(H):
-        U = Ef[H - b]                 # sites [e, d, dbar, e'] on row b's up legs (flipped: down legs)
+        U = Ef[H - b]                 # sites [e, u, ubar, e'] on row b's up legs (flipped: down legs)
         D = E[b + 1]                  # sites [f, d, dbar, f'] on row b's down legs
-
-        def transfer(c, op):
-            t = tns.T[b][c]                                              # s, u, l, d, r
-            s = t.shape[0]
-            o = np.eye(s, dtype=np.complex128) if (op is None or s == 1) else op
-            # T[e l lb f, e' r rb f'] = U[e,u,ub,e'] t[s,u,l,d,r] o[s,s'] conj t[s',ub,lb,db,rb] D[f,d,db,f']
-            X = np.einsum("aubA,sulDr,st,tbmEq,fDEF->almfArqF", U[c], t, o, t.conj(), D[c], optimize=True)
-            sh = X.shape
-            return X.reshape(sh[0] * sh[1] * sh[2] * sh[3], sh[4] * sh[5] * sh[6] * sh[7])
-
-        I = [transfer(c, None) for c in range(W)]
-        left = [np.ones((1,), dtype=np.complex128)]
+        T = tns.T[b]
+        ident = [np.eye(T[c].shape[0], dtype=np.complex128) for c in range(W)]
+        left = [np.ones((1, 1, 1, 1), dtype=np.complex128)]
         for c in range(W):
-            left.append(left[-1] @ I[c])
-        right = [np.ones((1,), dtype=np.complex128)] * (W + 1)
+            left.append(_grow_left(left[c], U[c], T[c], ident[c], D[c]))
+        right = [None] * (W + 1)
+        right[W] = np.ones((1, 1, 1, 1), dtype=np.complex128)
         for c in range(W - 1, -1, -1):
-            right[c] = I[c] @ right[c + 1]
-        norm = left[W].reshape(()).item()
+            right[c] = _grow_right(right[c + 1], U[c], T[c], ident[c], D[c])
+        # A truncated environment makes the contracted values slightly complex; the ratio
+        # of real parts is the one the sampler's conditionals use (q = Re rho_0 /
+        # Re(rho_0 + rho_1)), so marginals and conditionals are the same functional.
+        norm = float(np.real(left[W].reshape(()).item()))
         qs = [(c, int(tns.cell_qubit[b, c])) for c in range(W) if tns.cell_qubit[b, c] >= 0]
-        T1 = {c: transfer(c, P[1]) for c, _ in qs}
-        for c, q in qs:
-            one[q] = float(np.real((left[c] @ T1[c] @ right[c + 1]).item() / norm))
-            two[q, q] = one[q]
         for i, (ci, qi) in enumerate(qs):
-            v = left[ci] @ T1[ci]
-            for cj, qj in qs[i + 1:]:
-                for c in range(ci + 1, cj):
-                    v = v @ I[c]
-                val = float(np.real((v @ T1[cj] @ right[cj + 1]).item() / norm))
-                two[qi, qj] = two[qj, qi] = val
-                v = v @ I[cj]
-                ci = cj
+            v = _grow_left(left[ci], U[ci], T[ci], P1, D[ci])
+            one[qi] = float(np.real(np.sum(v * right[ci + 1]))) / norm
+            two[qi, qi] = one[qi]
+            if not pairs:
+                continue
+            for c in range(ci + 1, W):
+                q = int(tns.cell_qubit[b, c])
+                if q >= 0:
+                    val = float(np.real(np.sum(_grow_left(v, U[c], T[c], P1, D[c]) * right[c + 1]))) / norm
+                    two[qi, q] = two[q, qi] = val
+                v = _grow_left(v, U[c], T[c], ident[c], D[c])
     return one, two
 
 

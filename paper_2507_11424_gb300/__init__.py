@@ -117,6 +117,17 @@ class TNSState:
         check(self.lib.tns_log_norm(self._h, int(chi_b), C.byref(v)), "tns_log_norm")
         return v.value
 
+    def direct_marginals(self, chi_b: int, pairs: bool = True):
+        """(one [n], two [n, n] or None): <n_q> and same-row <n_q n_q'> by boundary-MPS contraction."""
+        if self.n is None:
+            raise ValueError("number of qubits unknown: set .n after load_file")
+        n = self.n
+        one = np.zeros(n, dtype=np.float64)
+        two = np.zeros((n, n), dtype=np.float64) if pairs else None
+        check(self.lib.tns_direct_marginals(self._h, int(chi_b), _ptr(one), _ptr(two) if pairs else None),
+              "tns_direct_marginals")
+        return one, two
+
     def set_precision(self, prec: str):
         check(self.lib.tns_set_precision(self._h, PREC[prec]), "tns_set_precision")
 

@@ -136,9 +136,10 @@ static void free_state(tns_state* s) {
   if (s->msg_new_arena) cudaFree(s->msg_new_arena);
   for (auto p : s->work_cells)
     if (p) cudaFree(p);
-  for (auto& E : s->env.E)
-    for (auto p : E.site)
-      if (p) cudaFree(p);
+  for (auto* ec : {&s->env, &s->env_top})
+    for (auto& E : ec->E)
+      for (auto p : E.site)
+        if (p) cudaFree(p);
   s->ws.release();
 }
 
@@ -308,6 +309,11 @@ extern "C" tns_status tns_log_fidelity(const tns_state* s, double* log_f) {
 extern "C" tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* out) {
   if (!s || !out || chi_b < 1) { set_error("invalid argument to tns_log_norm"); return TNS_ERR_ARG; }
   return log_norm(s, chi_b, out);
+}
+
+extern "C" tns_status tns_direct_marginals(tns_state* s, int32_t chi_b, double* one_host, double* two_host) {
+  if (!s || !one_host || chi_b < 1) { set_error("invalid argument to tns_direct_marginals"); return TNS_ERR_ARG; }
+  return direct_marginals(s, chi_b, one_host, two_host);
 }
 
 extern "C" tns_status tns_set_precision(tns_state* s, tns_prec prec) {

@@ -9,6 +9,9 @@
 namespace tns {
 
 static constexpr int JAC_THREADS = 256;
+// The eigensolver applies up to n/2 independent rotations per round, one warp each:
+// 32 warps keep the rotation phases short at the truncation sizes (n ~ 100).
+static constexpr int EIG_THREADS = 1024;
 static constexpr int MAX_SWEEPS = 40;
 static constexpr size_t SMEM_LIMIT = 200 * 1024;
 
@@ -61,7 +64,7 @@ template <> struct JacTol<float> { static constexpr float REL = 3e-7f, FLOOR = 1
 // T = double: the FP64 solver.  T = float: the same algorithm in FP32 (complex64
 // input), eigenvalues and eigenvectors written widened to FP64 storage.
 template <typename T>
-__global__ void __launch_bounds__(JAC_THREADS)
+__global__ void __launch_bounds__(EIG_THREADS)
 eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, double* lam, cd* Vout, long long sV,
             typename CplxOf<T>::type* work, int* status, int use_smem, int* sweeps_out) {
   typedef typename CplxOf<T>::type C;
@@ -69,7 +72,7 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
   __shared__ T cs_c[256], cs_s[256], cs_d[256];
   __shared__ C cs_e[256];
   __shared__ int cs_p[256], cs_q[256];
-  __shared__ T red[JAC_THREADS / 32];
+  __shared__ T red[EIG_THREADS / 32];
   __shared__ T floor_s;
   __shared__ int nrot;
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -92,7 +95,7 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
   __syncthreads();
   if (tid == 0) {
     T t = 0;
-    for (int w = 0; w < JAC_THREADS / 32; ++w) t += red[w];
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += red[w];
     floor_s = JacTol<T>::FLOOR * sqrt(t);     // absolute floor below which a pair counts as rotated
   }
   __syncthreads();
@@ -329,14 +332,22 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
   }
   for (int i = tid; i < n; i += blockDim.x) L[i * n + i].x += sft;
   __syncthreads();
+  __shared__ int broke;
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
+      // Every pivot of G + sft I (G PSD) is >= sft in exact arithmetic.  A smaller
+      // computed pivot means the Gram's rounding has made it indefinite in this
+      // direction: the pivot is set to sqrt(sft) and the column decoupled from the
+      // rest (zeroed below the diagonal), so the factor and its inverse stay bounded
+      // by 1/sqrt(sft) instead of growing through the remaining columns.
       T d = L[j * n + j].x;
-      L[j * n + j] = mk(sqrt(d > sft * (T)1e-3 ? d : sft), (T)0);
+      broke = !(d > sft);
+      L[j * n + j] = mk(sqrt(broke ? sft : d), (T)0);
     }
     __syncthreads();
     const T inv = 1 / L[j * n + j].x;
-    for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i * n + j] = cscale(L[i * n + j], inv);
+    for (int i = j + 1 + tid; i < n; i += blockDim.x)
+      L[i * n + j] = broke ? mk((T)0, (T)0) : cscale(L[i * n + j], inv);
     __syncthreads();
     const int m = n - j - 1;
     for (int idx = tid; idx < m * m; idx += blockDim.x) {        // trailing lower triangle
@@ -365,22 +376,25 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
 cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
                            cudaStream_t st) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
-  const bool f32 = !g_f64 && !w_f64;               // complex64 in and out: factorise in FP32
-  size_t bytes = (size_t)2 * n * n * (f32 ? sizeof(cf) : sizeof(cd));
+  // Complex64 in and out (the mixed path's CholeskyQR passes): the factorisation and
+  // the triangular inverse still run in FP64.  In FP32 their rounding (~n eps_32 of
+  // the largest pivot) reaches the shifts used at n ~ 100 and the inverse blows up.
+  const bool f32 = !g_f64 && !w_f64;
+  size_t bytes = (size_t)2 * n * n * sizeof(cd);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
   const size_t sm = use_smem ? bytes : 0;
   cudaError_t ea = cudaSuccess;
   if (w_f64 && g_f64) ea = smem_optin((const void*)chol_w_kernel<cd, cd, double>, (int)SMEM_LIMIT);
   else if (g_f64) ea = smem_optin((const void*)chol_w_kernel<cf, cd, double>, (int)SMEM_LIMIT);
-  else if (f32) ea = smem_optin((const void*)chol_w_kernel<cf, cf, float>, (int)SMEM_LIMIT);
+  else if (f32) ea = smem_optin((const void*)chol_w_kernel<cf, cf, double>, (int)SMEM_LIMIT);
   if (ea != cudaSuccess) return ea;
   if (w_f64 && g_f64)
     chol_w_kernel<cd, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, (cd*)work, use_smem);
   else if (g_f64)
     chol_w_kernel<cf, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cf*)W, (cd*)work, use_smem);
   else if (f32)
-    chol_w_kernel<cf, cf, float><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, (cf*)work, use_smem);
+    chol_w_kernel<cf, cf, double><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, (cd*)work, use_smem);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -398,7 +412,7 @@ cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double*
   if (!use_smem && !work) return cudaErrorInvalidValue;
   cudaError_t ea = smem_optin((const void*)eigh_kernel<double>, (int)SMEM_LIMIT);
   if (ea != cudaSuccess) return ea;
-  eigh_kernel<double><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
+  eigh_kernel<double><<<batch, EIG_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
                                                                         use_smem, sweeps_out);
   return cudaGetLastError();
 }
@@ -413,7 +427,7 @@ cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batc
   if (!use_smem && !work) return cudaErrorInvalidValue;
   cudaError_t ea = smem_optin((const void*)eigh_kernel<float>, (int)SMEM_LIMIT);
   if (ea != cudaSuccess) return ea;
-  eigh_kernel<float><<<batch, JAC_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
+  eigh_kernel<float><<<batch, EIG_THREADS, use_smem ? bytes : 0, st>>>(A, sA, lda, n, lam, V, sV, work, status,
                                                                        use_smem, sweeps_out);
   return cudaGetLastError();
 }

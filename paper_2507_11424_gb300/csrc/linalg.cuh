@@ -26,9 +26,8 @@ bool jacobi_fits_smem_f32(int n);
 // Orthonormalising map from a Gram matrix: W = L^{-H} with
 // L L^H = G + shift * max_i G_ii * I, batched n x n (contiguous).  G complex128
 // (g_f64) or complex64, W complex128 (w_f64) or complex64.  The factorisation runs
-// in FP64 unless both are complex64 (the mixed path's shifted CholeskyQR passes),
-// then in FP32.  work: >= batch * 2 n^2 complex of the factorisation's precision
-// when !chol_fits_smem(n).
+// in FP64 for every combination.  work: >= batch * 2 n^2 complex128 when
+// !chol_fits_smem(n).
 cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
                            cudaStream_t st);
 bool chol_fits_smem(int n);

@@ -22,9 +22,14 @@
 
 namespace tns {
 
+// Shifts of the Cholesky orthonormalisation, relative to the largest diagonal entry of
+// the Gram matrix.  In the mixed path the Gram matrices are FP32 sums over up to ~10^4
+// rows, whose rounding (~sqrt(rows) eps_32 ~ 10^-5) must stay below the shift of every
+// pass, or the shifted Gram can be indefinite; the later passes restore orthonormality
+// to that level.
 static constexpr double ORTH_SHIFT_FP64 = 1e-14;
 static constexpr double ORTH_SHIFT_CQR_FIRST = 1e-5;
-static constexpr double ORTH_SHIFT_CQR_NEXT = 1e-7;
+static constexpr double ORTH_SHIFT_CQR_NEXT = 1e-5;
 
 static inline int nblk(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 1 << 20); }
 
@@ -542,9 +547,10 @@ static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
 // Q = orthonormal basis of range(Y) for each batch entry (Y, Q: S x M x kk).
 // FP64 path: W = L^{-H} with L L^H = Y^H Y + 1e-14 max_i G_ii (the shift only
 // regularises rank-deficient Y), Q = Y W.  Mixed path: shifted CholeskyQR3 in
-// FP32 (Gram and products in FP32, the kk x kk Cholesky in FP64): a first pass
-// with shift 1e-5 gives a well-conditioned basis of the same range, two more
-// passes restore orthonormality to FP32 accuracy without damping any direction.
+// FP32 (Gram and products in FP32, the kk x kk Cholesky in FP64), every pass with
+// shift 1e-5: the first gives a well-conditioned basis of the same range, the two
+// more restore orthonormality to ~1e-5 (directions with Gram eigenvalue below the
+// shift are damped, not lost).
 static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void* Qout, bool span_only = false) {
   tns_state* s = cx.s;
   void *G, *Wm;
@@ -771,14 +777,18 @@ static void free_mps(StoredMPS& m) {
   m.site.clear();
 }
 
-// Bottom norm environments E[b], b = H..0 (E[0] gives <psi|psi>), at rank R.
-static tns_status build_envs(Ctx& cx_in) {
+// Bottom norm environments E[b], b = H..0 (E[0] gives <psi|psi>), at rank R.  With
+// top = true, the same construction on the state read upside down (row b of that
+// frame is row H-1-b, up and down legs exchanged): Et[H-b] is then the environment
+// of rows 0..b-1 on the up legs of row b.  Test matrices are keyed by the row index
+// of the frame the environments are built in.
+static tns_status build_envs(Ctx& cx_in, bool top = false) {
   // environment test matrices use key 0, independent of the sampling seed
   Ctx cx = cx_in;
   cx.seed = 0;
   tns_state* s = cx.s;
   cx.q = s->rf_q_env;
-  EnvCache& ec = s->env;
+  EnvCache& ec = top ? s->env_top : s->env;
   const int prec = cx.f64 ? 0 : 1;
   if (ec.valid && ec.chi_b == cx.R && ec.prec == prec && ec.version == s->version && ec.p == cx.p && ec.q == cx.q)
     return TNS_OK;
@@ -804,11 +814,13 @@ static tns_status build_envs(Ctx& cx_in) {
   TNS_TRY_CUDA(cudaMemsetAsync(dlog, 0, sizeof(double), cx.st));
   StoredMPS Z;
   const long long R = cx.R;
+  const char KU = top ? 'd' : 'u', KD = top ? 'u' : 'd', BU = top ? 'D' : 'U', BD = top ? 'U' : 'D';
   for (int b = H - 1; b >= 0; --b) {
+    const int r = top ? H - 1 - b : b;      // the grid row absorbed at this step
     // capacity per site: R * phys * R
     long long chi = 1;
     for (int c = 0; c < W; ++c)
-      for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, s->cell[s->cidx(b, c)].dim[leg]);
+      for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, s->cell[s->cidx(r, c)].dim[leg]);
     Z.site.assign(W, nullptr);
     for (int c = 0; c < W; ++c) {
       char nm[32];
@@ -818,7 +830,7 @@ static tns_status build_envs(Ctx& cx_in) {
     ZipSpec ket;
     ket.S = 1;
     ket.mview = [&, b](int j) { return mps_view(ec.E[b + 1], W, j, false, 'a', "Dd", 'b', 0, 0); };
-    ket.wview = [&, b](int j) { return cell_view(s, cx.f64, b, j, false, 's', 'u', 'l', 'd', 'r'); };
+    ket.wview = [&, r](int j) { return cell_view(s, cx.f64, r, j, false, 's', KU, 'l', KD, 'r'); };
     ket.out_phys = "suD";
     ket.stage = STAGE_ENV_KET;
     ket.row = b;
@@ -829,12 +841,12 @@ static tns_status build_envs(Ctx& cx_in) {
     StoredMPS& Eb = ec.E[b];
     Eb.site.assign(W, nullptr);
     long long Du = 1;
-    for (int c = 0; c < W; ++c) Du = std::max<long long>(Du, s->cell[s->cidx(b, c)].dim[LEG_U]);
+    for (int c = 0; c < W; ++c) Du = std::max<long long>(Du, s->cell[s->cidx(r, c)].dim[top ? LEG_D : LEG_U]);
     for (int c = 0; c < W; ++c) TNS_TRY_CUDA(cudaMalloc(&Eb.site[c], cx.esz * R * R * Du * Du));
     ZipSpec bra;
     bra.S = 1;
     bra.mview = [&](int j) { return mps_view(Z, W, j, true, 'a', "suD", 'b', 0, 0); };
-    bra.wview = [&, b](int j) { return cell_view(s, cx.f64, b, j, true, 's', 'U', 'l', 'D', 'r', true); };
+    bra.wview = [&, r](int j) { return cell_view(s, cx.f64, r, j, true, 's', BU, 'l', BD, 'r', true); };
     bra.out_phys = "Uu";  // E[b] sites [e][bra][ket][e']
     bra.stage = STAGE_ENV_BRA;
     bra.row = b;
@@ -1206,4 +1218,242 @@ tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, 
   return check_tc_error(cx);
 }
 
+// ------------------------------------------------------- direct marginals
+// Single-block reductions used between the row-contraction steps (vectors of at
+// most a few million entries; one block keeps the summation order fixed).
+template <typename C> __global__ void __launch_bounds__(1024) vec_normalize_kernel(C* v, long long n, double* nrm_out) {
+  __shared__ double red[1024];
+  double s2 = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s2 += cabs2(to_cd(v[i]));
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double nrm = sqrt(red[0]);
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) v[i] = from_cd<C>(cscale(to_cd(v[i]), inv));
+  if (threadIdx.x == 0) *nrm_out = nrm;
+}
+
+// out = sum_i a[i] b[i] (no conjugation: a full tensor contraction), as (re, im).
+template <typename C>
+__global__ void __launch_bounds__(1024) vec_dot_kernel(const C* a, const C* b, long long n, double* out) {
+  __shared__ double rr[1024], ri[1024];
+  double sr = 0.0, si = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const cd x = cmul(to_cd(a[i]), to_cd(b[i]));
+    sr += x.x;
+    si += x.y;
+  }
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { rr[threadIdx.x] += rr[threadIdx.x + o]; ri[threadIdx.x] += ri[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = rr[0]; out[1] = ri[0]; }
+}
+
+namespace {
+// One row of the norm network <psi|psi> between its top environment U (sites
+// [e][bra][ket][e']) and bottom environment D (sites [f][bra][ket][f']), contracted
+// site by site.  Vectors carry the four bonds cut between two columns:
+// [top env][ket horizontal][bra horizontal][bottom env].
+struct RowNet {
+  tns_state* s;
+  Ctx* cx;
+  int b;                          // grid row
+  const StoredMPS* U;             // top environment of row b (flipped-frame storage)
+  const StoredMPS* D;             // bottom environment E[b+1]
+  void *X1, *X2, *X3;             // intermediates
+
+  // ket (and, with proj, its bra) view of column c; proj = physical index fixed to 1
+  TView ket(int c, char ls, char lu, char ll, char ld, char lr, bool conj, bool proj) const {
+    TView v = cell_view(s, cx->f64, b, c, false, ls, lu, ll, ld, lr, conj);
+    if (proj && v.dim[0] == 2) {
+      v.ptr = (char*)v.ptr + cx->esz * v.stride[0];
+      v.dim[0] = 1;
+    }
+    return v;
+  }
+  long long bond(const StoredMPS& m, int c, bool right) const {
+    const int i = m.reversed ? s->W - 1 - c : c;
+    return m.bond[right ? (m.reversed ? i : i + 1) : (m.reversed ? i + 1 : i)];
+  }
+  // out[E][r][R][F] = sum in[e][l][L][f] U[e][B][u][E] psi[s][u][l][d][r] conj psi[s][B][L][Dd][R] D[f][Dd][d][F]
+  tns_status grow_left(int c, const void* in, void* out, bool proj) {
+    const Cell& cl = s->cell[s->cidx(b, c)];
+    const long long e = bond(*U, c, false), E = bond(*U, c, true), f = bond(*D, c, false), F = bond(*D, c, true);
+    const long long l = cl.dim[LEG_L], r = cl.dim[LEG_R], u = cl.dim[LEG_U], d = cl.dim[LEG_D];
+    const long long sp = (proj && cl.dim[0] == 2) ? 1 : cl.dim[0];
+    TView Uv = mps_view(*U, s->W, c, false, 'e', "Bu", 'E', 0, 0);
+    TView Dv = mps_view(*D, s->W, c, false, 'f', "Yd", 'F', 0, 0);
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(const_cast<void*>(in), "elLf", {e, l, l, f}), Uv,
+                           view(X1, "lLfBuE", {l, l, f, u, u, E}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X1, "lLfBuE", {l, l, f, u, u, E}), ket(c, 's', 'u', 'l', 'd', 'r', false, proj),
+                           view(X2, "LfBEsdr", {l, f, u, E, sp, d, r}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X2, "LfBEsdr", {l, f, u, E, sp, d, r}),
+                           ket(c, 's', 'B', 'L', 'Y', 'R', true, proj), view(X3, "fEdrYR", {f, E, d, r, d, r}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X3, "fEdrYR", {f, E, d, r, d, r}), Dv, view(out, "ErRF", {E, r, r, F}),
+                           cx->gp));
+    return TNS_OK;
+  }
+  // out[e][l][L][f] = sum U[e][B][u][E] psi[s][u][l][d][r] conj psi[s][B][L][Dd][R] D[f][Dd][d][F] in[E][r][R][F]
+  tns_status grow_right(int c, const void* in, void* out) {
+    const Cell& cl = s->cell[s->cidx(b, c)];
+    const long long e = bond(*U, c, false), E = bond(*U, c, true), f = bond(*D, c, false), F = bond(*D, c, true);
+    const long long l = cl.dim[LEG_L], r = cl.dim[LEG_R], u = cl.dim[LEG_U], d = cl.dim[LEG_D], sp = cl.dim[0];
+    TView Uv = mps_view(*U, s->W, c, false, 'e', "Bu", 'E', 0, 0);
+    TView Dv = mps_view(*D, s->W, c, false, 'f', "Yd", 'F', 0, 0);
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, Uv, view(const_cast<void*>(in), "ErRF", {E, r, r, F}),
+                           view(X1, "eBurRF", {e, u, u, r, r, F}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X1, "eBurRF", {e, u, u, r, r, F}), ket(c, 's', 'u', 'l', 'd', 'r', false, false),
+                           view(X2, "eBRFsld", {e, u, r, F, sp, l, d}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X2, "eBRFsld", {e, u, r, F, sp, l, d}),
+                           ket(c, 's', 'B', 'L', 'Y', 'R', true, false), view(X3, "eFldLY", {e, F, l, d, l, d}), cx->gp));
+    TNS_TRY_CUDA(pcontract(s, PC_ENV, view(X3, "eFldLY", {e, F, l, d, l, d}), Dv, view(out, "elLf", {e, l, l, f}),
+                           cx->gp));
+    return TNS_OK;
+  }
+};
+}  // namespace
+
+// Sample-free marginals <n_q> for every qubit and <n_q n_q'> for every pair in the
+// same grid row (Methods, expectation values from the boundary-MPS contraction of
+// <psi|psi>): row b is contracted exactly between its top and bottom environments
+// at rank chi_b, from the left and from the right, with P1 = |1><1| (the physical
+// index fixed to 1 in ket and bra) on the marginal's qubits.  Every partial vector
+// is stored at unit norm and its scale kept as a log on the host, so no contraction
+// over- or underflows.  one: host [n]; two: host [n][n] or NULL (NaN off the rows).
+tns_status direct_marginals(tns_state* s, int chi_b, double* one, double* two) {
+  Ctx cx;
+  TNS_TRY(make_ctx(s, chi_b, 0, cx));
+  TNS_TRY(build_envs(cx, false));
+  TNS_TRY(build_envs(cx, true));
+  const int H = s->H, W = s->W;
+  for (int q = 0; q < s->n; ++q) one[q] = NAN;
+  if (two)
+    for (long long i = 0; i < (long long)s->n * s->n; ++i) two[i] = NAN;
+  // workspace: vectors (R * chi * chi * R) and the three intermediates
+  long long chi = 1, rho = 1;
+  for (auto& c : s->cell)
+    for (int leg = 1; leg <= 4; ++leg) chi = std::max<long long>(chi, c.dim[leg]);
+  for (auto* ec : {&s->env, &s->env_top})
+    for (auto& E : ec->E) rho = std::max(rho, env_rank(E));
+  const long long vcap = rho * chi * chi * rho, xcap = 2 * rho * chi * chi * chi * chi * rho;
+  RowNet net;
+  net.s = s;
+  net.cx = &cx;
+  TNS_TRY(wsget(s, "dm_X1", cx.esz * xcap, &net.X1));
+  TNS_TRY(wsget(s, "dm_X2", cx.esz * xcap * chi, &net.X2));
+  TNS_TRY(wsget(s, "dm_X3", cx.esz * xcap, &net.X3));
+  std::vector<void*> left(W + 1), right(W + 1);
+  for (int c = 0; c <= W; ++c) {
+    char nm[32];
+    snprintf(nm, sizeof nm, "dm_L%d", c);
+    TNS_TRY(wsget(s, nm, cx.esz * vcap, &left[c]));
+    snprintf(nm, sizeof nm, "dm_R%d", c);
+    TNS_TRY(wsget(s, nm, cx.esz * vcap, &right[c]));
+  }
+  void *v0, *v1;
+  TNS_TRY(wsget(s, "dm_v0", cx.esz * vcap, &v0));
+  TNS_TRY(wsget(s, "dm_v1", cx.esz * vcap, &v1));
+  double* dscal;
+  TNS_TRY(wsget(s, "dm_scal", sizeof(double) * 2, (void**)&dscal));
+  // vector element counts at the cut left of column c (c = W: the trivial right end)
+  auto vlen = [&](const RowNet& rn, int c) -> long long {
+    if (c == 0 || c == W) return 1;
+    const Cell& cl = s->cell[s->cidx(rn.b, c)];
+    return rn.bond(*rn.U, c, false) * cl.dim[LEG_L] * cl.dim[LEG_L] * rn.bond(*rn.D, c, false);
+  };
+  auto normalize = [&](void* v, long long n, double* log_scale) -> tns_status {
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      vec_normalize_kernel<C><<<1, 1024, 0, cx.st>>>((C*)v, n, dscal);
+    });
+    s->launches++;
+    double h = 0.0;
+    TNS_TRY_CUDA(cudaMemcpyAsync(&h, dscal, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
+    TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+    *log_scale = h > 0.0 ? std::log(h) : -INFINITY;
+    return TNS_OK;
+  };
+  auto dot = [&](const void* a, const void* bb, long long n, double* re) -> tns_status {
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      vec_dot_kernel<C><<<1, 1024, 0, cx.st>>>((const C*)a, (const C*)bb, n, dscal);
+    });
+    s->launches++;
+    double h[2];
+    TNS_TRY_CUDA(cudaMemcpyAsync(h, dscal, sizeof(double) * 2, cudaMemcpyDeviceToHost, cx.st));
+    TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+    *re = h[0];
+    return TNS_OK;
+  };
+  for (int b = 0; b < H; ++b) {
+    net.b = b;
+    net.U = &s->env_top.E[H - b];
+    net.D = &s->env.E[b + 1];
+    std::vector<double> la(W + 1, 0.0), lb(W + 1, 0.0);
+    dispatch(cx.f64, [&](auto* tp) {
+      using C = std::remove_pointer_t<decltype(tp)>;
+      fill_kernel<C><<<1, 32, 0, cx.st>>>((C*)left[0], 1, 1.0);
+      fill_kernel<C><<<1, 32, 0, cx.st>>>((C*)right[W], 1, 1.0);
+    });
+    s->launches += 2;
+    for (int c = 0; c < W; ++c) {
+      TNS_TRY(net.grow_left(c, left[c], left[c + 1], false));
+      double g;
+      TNS_TRY(normalize(left[c + 1], vlen(net, c + 1), &g));
+      la[c + 1] = la[c] + g;
+    }
+    for (int c = W - 1; c >= 0; --c) {
+      TNS_TRY(net.grow_right(c, right[c + 1], right[c]));
+      double g;
+      TNS_TRY(normalize(right[c], vlen(net, c), &g));
+      lb[c] = lb[c + 1] + g;
+    }
+    const double log_norm = la[W];            // left[W] = <psi|psi> of this row's network, at unit norm
+    double zW;
+    TNS_TRY(dot(left[W], right[W], 1, &zW));
+    // <P> at columns (ci[, cj]) = e^{scales - log_norm} Re(v . right) / zW
+    for (int ci = 0; ci < W; ++ci) {
+      const int qi = s->cell[s->cidx(b, ci)].qubit;
+      if (qi < 0) continue;
+      TNS_TRY(net.grow_left(ci, left[ci], v0, true));
+      double gv;
+      TNS_TRY(normalize(v0, vlen(net, ci + 1), &gv));
+      double lv = la[ci] + gv, val;
+      TNS_TRY(dot(v0, right[ci + 1], vlen(net, ci + 1), &val));
+      one[qi] = std::exp(lv + lb[ci + 1] - log_norm) * val / zW;
+      if (!two) continue;
+      two[(long long)qi * s->n + qi] = one[qi];
+      void* vc = v0;
+      void* vn = v1;
+      for (int c = ci + 1; c < W; ++c) {
+        const int q = s->cell[s->cidx(b, c)].qubit;
+        if (q >= 0) {
+          TNS_TRY(net.grow_left(c, vc, vn, true));
+          double gp, vv;
+          TNS_TRY(normalize(vn, vlen(net, c + 1), &gp));
+          TNS_TRY(dot(vn, right[c + 1], vlen(net, c + 1), &vv));
+          const double x = std::exp(lv + gp + lb[c + 1] - log_norm) * vv / zW;
+          two[(long long)qi * s->n + q] = two[(long long)q * s->n + qi] = x;
+        }
+        if (c + 1 < W) {
+          TNS_TRY(net.grow_left(c, vc, vn, false));
+          double gi;
+          TNS_TRY(normalize(vn, vlen(net, c + 1), &gi));
+          lv += gi;
+          std::swap(vc, vn);
+        }
+      }
+    }
+  }
+  TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
+  return check_tc_error(cx);
+}
 }  // namespace tns

@@ -88,12 +88,13 @@ struct tns_state {
   long long version = 0;                // bumped whenever site tensors change
   long long launches = 0;
   tns::Workspace ws;
-  tns::EnvCache env;
+  tns::EnvCache env;                    // bottom environments E[b] (rows b..H-1)
+  tns::EnvCache env_top;                // top environments, built on the flipped frame
   tns::Profiler prof;
   std::vector<void*> work_cells;        // working-precision copies of the cell tensors
   int work_prec = -1;
   bool tensor_cores = true;             // mixed path: environment GEMMs on tcgen05
-  int rf_p = 64;                        // range-finder oversampling (k = chi_b + rf_p columns)
+  int rf_p = 48;                        // range-finder oversampling (k = chi_b + rf_p columns)
   int rf_q = 3;                         // subspace iterations of the sampler and amplitude zips
   int rf_q_env = 6;                     // subspace iterations of the norm-environment zips
   long long work_version = -1;
@@ -129,4 +130,5 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
                   double* logq, double* cond);
 tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase);
 tns_status log_norm(tns_state* s, int chi_b, double* out);
+tns_status direct_marginals(tns_state* s, int chi_b, double* one, double* two);
 }  // namespace tns

@@ -191,6 +191,8 @@ CONTRACTIONS = [
     ("Saec", (4, 12, 7, 12), "S", 0, "SasdA", (4, 12, 2, 5, 12), "", 0, "ScsAed"),        # stride-0 batch in A
     ("mk", (300, 40), "", 0, "nk", (200, 40), "", 0, "mn"),                               # BN = 256, ragged tiles
     ("km", (40, 300), "", 1, "kn", (40, 60), "", 0, "nm"),                                # transposed, BN = 128
+    ("mc", (1024, 264), "", 1, "me", (1024, 264), "", 0, "ce"),                           # Gram Y^H Y, n > 128
+    ("Smc", (2, 700, 136), "", 1, "Sme", (2, 700, 136), "", 0, "Sce"),                    # batched Gram
 ]
 
 
