@@ -163,6 +163,18 @@ tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* log_norm);
  */
 tns_status tns_direct_marginals(tns_state* s, int32_t chi_b, double* one_host, double* two_host);
 
+/*
+ * tns_set_graphs -- 1 (default): tns_sample and tns_sample_replay run each chunk's
+ * launch sequence (several thousand kernels at the 10x10 workload) from a CUDA
+ * graph.  The first chunk of a given shape runs eagerly, the second is captured,
+ * later ones replay the graph; the seed, first sample index and output buffers are
+ * read on the device, so one graph serves every call.  A graph is rebuilt when the
+ * state, its precision, rank, compression settings, chunk size or any internal
+ * buffer changes.  Results are identical with and without graphs.  0: always
+ * launch eagerly (also the case while kernel timing is on).
+ */
+tns_status tns_set_graphs(tns_state* s, int32_t enable);
+
 /* Select the precision of later tns_sample / tns_amplitude calls. */
 tns_status tns_set_precision(tns_state* s, tns_prec prec);
 

@@ -152,6 +152,10 @@ class TNSState:
         check(self.lib.tns_set_compression(self._h, int(oversample), int(power_iters), int(env_power_iters)),
               "tns_set_compression")
 
+    def set_graphs(self, enable: bool):
+        """Replay the sampler's per-chunk launch sequence from CUDA graphs (see tns_set_graphs)."""
+        check(self.lib.tns_set_graphs(self._h, 1 if enable else 0), "tns_set_graphs")
+
     def set_tensor_cores(self, enable: bool):
         check(self.lib.tns_set_tensor_cores(self._h, 1 if enable else 0), "tns_set_tensor_cores")
 

@@ -33,6 +33,7 @@ cudaError_t Workspace::get(const std::string& name, size_t bytes, void** out) {
     if (e != cudaSuccess) return e;
     cudaFree(it->second.first);
     slots.erase(it);
+    ++gen;
   }
   void* p = nullptr;
   size_t nb = bytes < 256 ? 256 : bytes;
@@ -136,6 +137,9 @@ static void free_state(tns_state* s) {
   if (s->msg_new_arena) cudaFree(s->msg_new_arena);
   for (auto p : s->work_cells)
     if (p) cudaFree(p);
+  for (auto& g : s->graphs)
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+  s->graphs.clear();
   for (auto* ec : {&s->env, &s->env_top})
     for (auto& E : ec->E)
       for (auto p : E.site)
@@ -325,6 +329,12 @@ extern "C" tns_status tns_set_precision(tns_state* s, tns_prec prec) {
 extern "C" tns_status tns_set_tensor_cores(tns_state* s, int32_t enable) {
   if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
   s->tensor_cores = enable != 0;
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_set_graphs(tns_state* s, int32_t enable) {
+  if (!s) { set_error("state is NULL"); return TNS_ERR_ARG; }
+  s->use_graphs = enable != 0;
   return TNS_OK;
 }
 

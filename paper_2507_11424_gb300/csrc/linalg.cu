@@ -296,6 +296,8 @@ svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout
 // the columns of L^{-1} (one thread per column).  Used so that Y W has
 // orthonormal columns when G = Y^H Y; the shift keeps it well defined for
 // rank-deficient Y and damps directions below shift * max G_ii smoothly.
+// use_smem: 2 = L and X = L^{-1} in shared memory, 1 = L in shared memory and X in
+// work (n^2 per matrix), 0 = both in work (2 n^2 per matrix).
 template <typename C, typename GIN, typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
 chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::type* work, int use_smem) {
@@ -304,8 +306,9 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
   __shared__ T red[JAC_THREADS / 32];
   __shared__ T sh_s;
   const int b = blockIdx.x, tid = threadIdx.x;
-  CT* L = use_smem ? reinterpret_cast<CT*>(smraw4) : work + (long long)b * 2 * n * n;
-  CT* X = L + (long long)n * n;
+  const long long nn = (long long)n * n;
+  CT* L = use_smem ? reinterpret_cast<CT*>(smraw4) : work + (long long)b * 2 * nn;
+  CT* X = use_smem == 2 ? L + nn : (use_smem == 1 ? work + (long long)b * nn : L + nn);
   const GIN* G = Gin + (long long)b * n * n;
   T mx = 0;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
@@ -374,26 +377,32 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
 }
 
 cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool fp32_factor) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   // Complex64 in and out (the mixed path's CholeskyQR passes): the factorisation and
-  // the triangular inverse still run in FP64.  In FP32 their rounding (~n eps_32 of
-  // the largest pivot) reaches the shifts used at n ~ 100 and the inverse blows up.
-  const bool f32 = !g_f64 && !w_f64;
-  size_t bytes = (size_t)2 * n * n * sizeof(cd);
-  int use_smem = bytes <= SMEM_LIMIT;
-  if (!use_smem && !work) return cudaErrorInvalidValue;
-  const size_t sm = use_smem ? bytes : 0;
+  // the triangular inverse run in FP64 unless fp32_factor (passes where only the span
+  // of the result matters).  In FP32 their rounding (~n eps_32 of the largest pivot)
+  // reaches the shifts used at n ~ 100, which the pivot guard then absorbs.
+  const bool c64 = !g_f64 && !w_f64;
+  const bool f32 = c64 && fp32_factor;
+  const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
+  const size_t nn = (size_t)n * n * esz;
+  const int use_smem = 2 * nn <= SMEM_LIMIT ? 2 : (nn <= SMEM_LIMIT ? 1 : 0);
+  if (use_smem < 2 && !work) return cudaErrorInvalidValue;
+  const size_t sm = use_smem == 2 ? 2 * nn : (use_smem == 1 ? nn : 0);
   cudaError_t ea = cudaSuccess;
   if (w_f64 && g_f64) ea = smem_optin((const void*)chol_w_kernel<cd, cd, double>, (int)SMEM_LIMIT);
   else if (g_f64) ea = smem_optin((const void*)chol_w_kernel<cf, cd, double>, (int)SMEM_LIMIT);
-  else if (f32) ea = smem_optin((const void*)chol_w_kernel<cf, cf, double>, (int)SMEM_LIMIT);
+  else if (f32) ea = smem_optin((const void*)chol_w_kernel<cf, cf, float>, (int)SMEM_LIMIT);
+  else if (c64) ea = smem_optin((const void*)chol_w_kernel<cf, cf, double>, (int)SMEM_LIMIT);
   if (ea != cudaSuccess) return ea;
   if (w_f64 && g_f64)
     chol_w_kernel<cd, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cd*)W, (cd*)work, use_smem);
   else if (g_f64)
     chol_w_kernel<cf, cd, double><<<batch, JAC_THREADS, sm, st>>>((const cd*)G, n, shift, (cf*)W, (cd*)work, use_smem);
   else if (f32)
+    chol_w_kernel<cf, cf, float><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, (cf*)work, use_smem);
+  else if (c64)
     chol_w_kernel<cf, cf, double><<<batch, JAC_THREADS, sm, st>>>((const cf*)G, n, shift, (cf*)W, (cd*)work, use_smem);
   else
     return cudaErrorInvalidValue;

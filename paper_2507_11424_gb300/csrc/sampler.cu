@@ -47,7 +47,9 @@ template <typename C> __global__ void fill_kernel(C* out, long long n, double v)
 // Range-finder test matrix Omega[i][j] (n x kk): Philox counter (i, j, row*4096+site,
 // 0x80000000 | stage), key = seed; Re from words 0,1 and Im from words 2,3, each 2u-1.
 template <typename C>
-__global__ void omega_kernel(C* out, int n, int kk, uint64_t seed, int stage, int row, int site) {
+__global__ void omega_kernel(C* out, int n, int kk, uint64_t seed_arg, const uint64_t* seed_dev, int stage, int row,
+                             int site) {
+  const uint64_t seed = seed_dev ? *seed_dev : seed_arg;
   long long tot = (long long)n * kk;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -155,6 +157,18 @@ template <typename C> __global__ void normalize_kernel(C* F, long long n) {
   for (long long i = threadIdx.x; i < n; i += blockDim.x) F[b * n + i] = from_cd<C>(cscale(to_cd(F[b * n + i]), inv));
 }
 
+// Per-call arguments of the sampler's chunk, read on the device so that one captured
+// launch sequence serves every call: the sampling seed (also the key of the
+// range-finder test matrices), the chunk's first sample index and the output buffers.
+struct SampleCall {
+  uint64_t seed;
+  long long sample0;
+  uint8_t* bits;
+  const uint8_t* forced;
+  double* logq;
+  double* cond;
+};
+
 // Conditional marginals of one qubit for every sample of the chunk, in two
 // kernels with MARG_SPLIT blocks per sample (enough blocks to fill the GPU at any
 // chunk size):
@@ -204,9 +218,14 @@ template <typename C>
 __global__ void __launch_bounds__(256)
 marginal_draw_kernel(const double* __restrict__ part, const C* __restrict__ G, int P, long long nel,
                      const C* __restrict__ Kp, long long kstride, int ka, int Dd, int kb, C* __restrict__ Lnext,
-                     C* __restrict__ mnext, uint8_t* bits, const uint8_t* forced, int n_sites, int qubit, double* logq,
-                     double* cond, uint64_t seed, long long sample0) {
+                     C* __restrict__ mnext, const SampleCall* __restrict__ call, int n_sites, int qubit) {
   const long long sidx = blockIdx.y;
+  uint8_t* bits = call->bits;
+  const uint8_t* forced = call->forced;
+  double* logq = call->logq;
+  double* cond = call->cond;
+  const uint64_t seed = call->seed;
+  const long long sample0 = call->sample0;
   const int k = blockIdx.x;
   __shared__ int xs;
   __shared__ double invs;
@@ -442,6 +461,7 @@ struct Ctx {
   size_t esz;
   uint64_t seed;
   int R;
+  const uint64_t* seed_dev = nullptr;   // when set, kernels read the seed here (graph replays)
   int p = 8;      // range-finder oversampling: k = R + p columns
   int q = 1;      // subspace iterations (T T^H applications)
 };
@@ -466,6 +486,7 @@ static tns_status ensure_work_cells(tns_state* s, bool f64) {
     s->launches++;
   }
   s->work_prec = want;
+  s->work_gen++;
   s->work_version = s->version;
   return TNS_OK;
 }
@@ -558,25 +579,25 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
   TNS_TRY(wsget(s, "z_W", cx.esz * S * kk * kk, &Wm));
   cd* work = nullptr;
   if (!chol_fits_smem(kk)) TNS_TRY(wsget(s, "z_cwork", sizeof(cd) * S * 2 * kk * kk, (void**)&work));
-  auto pass = [&](void* src, void* dst, double shift) -> tns_status {
+  auto pass = [&](void* src, void* dst, double shift, bool fp32_factor) -> tns_status {
     TNS_TRY_CUDA(pgram(s, cx.gp, src, S, M, kk, G));
     cudaEvent_t ev = s->prof.begin(cx.st);
-    TNS_TRY_CUDA(chol_w_batched(G, cx.f64, kk, (int)S, shift, Wm, cx.f64, work, cx.st));
+    TNS_TRY_CUDA(chol_w_batched(G, cx.f64, kk, (int)S, shift, Wm, cx.f64, work, cx.st, fp32_factor));
     s->prof.end(PC_EIGH, ev, 0.0, cx.st);
     s->launches++;
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(src, "Smc", {S, M, kk}), view(Wm, "Sce", {S, kk, kk}),
                            view(dst, "Sme", {S, M, kk}), cx.gp));
     return TNS_OK;
   };
-  if (cx.f64) return pass(Y, Qout, ORTH_SHIFT_FP64);
-  // between subspace iterations only the span matters: one pass gives a basis of the
-  // same range that is orthonormal to ~eps * cond(Y)^2
-  if (span_only) return pass(Y, Qout, ORTH_SHIFT_CQR_FIRST);
+  if (cx.f64) return pass(Y, Qout, ORTH_SHIFT_FP64, false);
+  // between subspace iterations only the span matters: one pass, factorised in FP32,
+  // gives a bounded basis of the same range
+  if (span_only) return pass(Y, Qout, ORTH_SHIFT_CQR_FIRST, true);
   void* tmp;
   TNS_TRY(wsget(s, "z_Q2", cx.esz * S * M * kk, &tmp));
-  TNS_TRY(pass(Y, Qout, ORTH_SHIFT_CQR_FIRST));
-  TNS_TRY(pass(Qout, tmp, ORTH_SHIFT_CQR_NEXT));
-  return pass(tmp, Qout, ORTH_SHIFT_CQR_NEXT);
+  TNS_TRY(pass(Y, Qout, ORTH_SHIFT_CQR_FIRST, false));
+  TNS_TRY(pass(Qout, tmp, ORTH_SHIFT_CQR_NEXT, false));
+  return pass(tmp, Qout, ORTH_SHIFT_CQR_NEXT, false);
 }
 
 // Rank-R factorisation T = K C of each batch entry (T: S x M x N): randomized
@@ -619,7 +640,7 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
     TNS_TRY(wsget(s, "z_om", cx.esz * N * kk, &om));
     dispatch(cx.f64, [&](auto* tp) {
       using C = std::remove_pointer_t<decltype(tp)>;
-      omega_kernel<C><<<nblk(N * kk), 256, 0, cx.st>>>((C*)om, (int)N, kk, cx.seed, stage, row, site);
+      omega_kernel<C><<<nblk(N * kk), 256, 0, cx.st>>>((C*)om, (int)N, kk, cx.seed, cx.seed_dev, stage, row, site);
     });
     s->launches++;
     TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(T, "Smn", {S, M, N}), view(om, "nc", {N, kk}), view(Y, "Smc", {S, M, kk}),
@@ -786,6 +807,7 @@ static tns_status build_envs(Ctx& cx_in, bool top = false) {
   // environment test matrices use key 0, independent of the sampling seed
   Ctx cx = cx_in;
   cx.seed = 0;
+  cx.seed_dev = nullptr;
   tns_state* s = cx.s;
   cx.q = s->rf_q_env;
   EnvCache& ec = top ? s->env_top : s->env;
@@ -880,6 +902,7 @@ static tns_status build_envs(Ctx& cx_in, bool top = false) {
   }
   ec.log_norm = lg + 0.5 * std::log(zr * zr + zi * zi);
   ec.valid = true;
+  s->env_builds++;
   ec.chi_b = cx.R;
   ec.prec = prec;
   ec.version = s->version;
@@ -1004,8 +1027,13 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   });
   s->launches++;
 
-  for (long long s0 = 0; s0 < n; s0 += chunk) {
-    const long long S = std::min(chunk, n - s0);
+  // The per-chunk launch sequence: everything in it depends on the state, the
+  // settings and the chunk size S only; the call's seed, first sample and output
+  // buffers come from the device block `dcall`.
+  SampleCall* dcall;
+  TNS_TRY(wsget(s, "s_call", sizeof(SampleCall), (void**)&dcall));
+  cx.seed_dev = &dcall->seed;
+  auto run_chunk = [&](long long S) -> tns_status {
     // m_0: trivial, shared by all samples
     StoredMPS mcur;
     mcur.reversed = false;
@@ -1107,7 +1135,7 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
                                                               mpart);
           marginal_draw_kernel<C><<<grid, 256, 0, cx.st>>>(
               mpart, (const C*)Gb, (int)P, nel, (const C*)Kp.site[j], kst, (int)ka, (int)Dd, (int)kb, (C*)Ln,
-              (C*)mnext.site[j], bits, forced, s->n, q < 0 ? 0 : q, logq, cond, cx.seed, s0);
+              (C*)mnext.site[j], dcall, s->n, q < 0 ? 0 : q);
         });
         s->launches++;
         s->prof.end(PC_MARG, mev, 0.0, cx.st);
@@ -1118,6 +1146,54 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
       mcur = mnext;
       mshared = false;
     }
+    return TNS_OK;
+  };
+  for (long long s0 = 0; s0 < n; s0 += chunk) {
+    const long long S = std::min(chunk, n - s0);
+    SampleCall hc{seed, s0, bits, forced, logq, cond};
+    static_assert(sizeof(SampleCall) <= sizeof(s->host_call), "call block staging");
+    memcpy(s->host_call, &hc, sizeof hc);
+    TNS_TRY_CUDA(cudaMemcpyAsync(dcall, s->host_call, sizeof hc, cudaMemcpyHostToDevice, cx.st));
+    if (!s->use_graphs || s->prof.on) {
+      TNS_TRY(run_chunk(S));
+      continue;
+    }
+    // everything the launch sequence depends on (buffer addresses included, through the
+    // generation counters of the workspace, environments and working copies)
+    const std::vector<long long> key = {s->version, R, S, cx.f64 ? 1 : 0, (long long)cx.gp, cx.p, cx.q,
+                                        s->tensor_cores ? 1 : 0, s->ws.gen, s->env_builds, s->work_gen};
+    auto it = s->graphs.find(key);
+    if (it == s->graphs.end()) {
+      if (!s->graph_seen.count(key)) {            // first time: run eagerly (sizes every buffer)
+        s->graph_seen.insert(key);
+        TNS_TRY(run_chunk(S));
+        continue;
+      }
+      const long long l0 = s->launches;
+      TNS_TRY_CUDA(cudaStreamBeginCapture(cx.st, cudaStreamCaptureModeThreadLocal));
+      tns_status rs = run_chunk(S);
+      cudaGraph_t g = nullptr;
+      cudaError_t ec = cudaStreamEndCapture(cx.st, &g);
+      if (rs != TNS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rs;
+      }
+      TNS_TRY_CUDA(ec);
+      tns_state::GraphEntry en;
+      en.launches = s->launches - l0;
+      s->launches = l0;
+      ec = cudaGraphInstantiate(&en.exec, g, 0);
+      cudaGraphDestroy(g);
+      TNS_TRY_CUDA(ec);
+      if (s->ws.gen != key[8]) {                   // a buffer moved during capture: do not keep it
+        cudaGraphExecDestroy(en.exec);
+        set_error("workspace changed while capturing the sampler's launch sequence");
+        return TNS_ERR_STATE;
+      }
+      it = s->graphs.emplace(key, en).first;
+    }
+    TNS_TRY_CUDA(cudaGraphLaunch(it->second.exec, cx.st));
+    s->launches += it->second.launches;
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
   s->prof.resolve();

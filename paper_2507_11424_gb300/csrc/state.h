@@ -1,6 +1,7 @@
 // Internal state of the tensor-network library (host side).
 #pragma once
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@ struct Cell {
 // Named, grow-only device buffers reused across calls.
 struct Workspace {
   std::map<std::string, std::pair<void*, size_t>> slots;
+  long long gen = 0;                    // bumped whenever a buffer is reallocated
   cudaError_t get(const std::string& name, size_t bytes, void** out);
   void release();
 };
@@ -97,6 +99,16 @@ struct tns_state {
   int rf_p = 48;                        // range-finder oversampling (k = chi_b + rf_p columns)
   int rf_q = 3;                         // subspace iterations of the sampler and amplitude zips
   int rf_q_env = 6;                     // subspace iterations of the norm-environment zips
+  // CUDA graphs of the sampler's per-chunk launch sequence, keyed by everything the
+  // sequence depends on (see sample()); a key seen once runs eagerly, the second time
+  // it is captured, then replayed.
+  bool use_graphs = true;
+  struct GraphEntry { cudaGraphExec_t exec = nullptr; long long launches = 0; };
+  std::map<std::vector<long long>, GraphEntry> graphs;
+  std::set<std::vector<long long>> graph_seen;
+  long long env_builds = 0;             // bumped when norm environments are rebuilt
+  long long work_gen = 0;               // bumped when the working-precision cell copies change
+  unsigned char host_call[64] = {};     // staging for the per-call parameter block
   long long work_version = -1;
 
   int cidx(int r, int c) const { return r * W + c; }

@@ -30,6 +30,7 @@
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
@@ -356,10 +357,64 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
   return cudaGetLastError();
 }
 
+// Tile width per shape class.  Outputs of up to 64 complex columns always take the
+// 128-column tile (a 256-column tile would be mostly padding).  Wider outputs take
+// whichever of 128 and 256 ran faster the first time the class was met: both widths
+// are launched once, timed with CUDA events on the caller's stream, and the choice is
+// frozen for the rest of the process.  Each output element accumulates the same MMA
+// sequence over K under either width, so the choice changes speed only (a test holds
+// the two bit-identical).  During stream capture an untuned class takes the 256 tile.
+namespace {
+std::mutex g_tile_mu;
+std::map<std::vector<long long>, int> g_tile;
+int g_force_bn = 0;                       // testing: 128 or 256 forces the width
+}
+
+void tc_force_tile(int bn) {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_force_bn = bn;
+}
+
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st) {
   if (!tc_available() || a.e.M < 1 || a.e.N < 1 || a.Kr < 1 || a.nbatch < 1) return cudaErrorNotSupported;
   if (tc_tile_n(a.e.N) == 128) return launch_bn<128>(op, a, st);
-  return launch_bn<256>(op, a, st);
+  int forced = 0;
+  std::vector<long long> key;
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    forced = g_force_bn;
+    if (!forced) {
+      // class: row count to a power of two, exact N and K, operand sharing and batching
+      const long long rows = a.merged ? a.nbatch * a.e.M : a.e.M;
+      int rl = 0;
+      while ((1LL << rl) < rows) ++rl;
+      key = {rl, a.e.N, a.Kr, a.merged, a.a_batched, a.b_batched, a.merged ? 1 : a.nbatch};
+      auto it = g_tile.find(key);
+      if (it != g_tile.end()) forced = it->second;
+    }
+  }
+  if (forced == 128) return launch_bn<128>(op, a, st);
+  if (forced == 256) return launch_bn<256>(op, a, st);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return launch_bn<256>(op, a, st);
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return launch_bn<256>(op, a, st);
+  cudaError_t e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = launch_bn<128>(op, a, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = launch_bn<256>(op, a, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+  float t128 = 0.f, t256 = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t128, ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t256, ev[1], ev[2]);
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tile.emplace(key, t128 < t256 ? 128 : 256);
+  return cudaSuccess;
 }
 
 int* tc_error_flag() {

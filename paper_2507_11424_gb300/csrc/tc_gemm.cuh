@@ -70,6 +70,8 @@ bool tma_map_2d(CUtensorMap* map, bool bf16, const void* ptr, long long rows, lo
                 int box_cols, int box_rows);
 // cudaErrorNotSupported when the shape or alignment does not fit the kernel.
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st);
+// Testing: force the tile width of later launches (128 or 256; 0 = the tuned choice).
+void tc_force_tile(int bn);
 // Per-device error flag shared by every tensor-core launch (lazily allocated).
 int* tc_error_flag();
 

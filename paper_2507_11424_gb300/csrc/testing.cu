@@ -150,6 +150,12 @@ extern "C" tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const flo
   return TNS_OK;
 }
 
+extern "C" tns_status tns_test_tc_tile(int32_t bn) {
+  if (bn != 0 && bn != 128 && bn != 256) { set_error("tile width must be 0, 128 or 256"); return TNS_ERR_ARG; }
+  tc_force_tile(bn);
+  return TNS_OK;
+}
+
 extern "C" tns_status tns_test_contract(const char* labels_a, const int64_t* dims_a, const int64_t* strides_a,
                                         int32_t conj_a, const void* A, const char* labels_b, const int64_t* dims_b,
                                         const int64_t* strides_b, int32_t conj_b, const void* B, const char* labels_c,

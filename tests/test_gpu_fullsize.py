@@ -37,8 +37,10 @@ def state(tmp_path_factory):
     build.build()
     gold = dict(np.load(GOLD))
     t, cfg, _ = build_state()
-    # the rebuilt oracle state is the one the reference was computed on
-    assert abs(t.log_fidelity - float(gold["log_fidelity"])) < 1e-9
+    # the rebuilt oracle state is the one the reference was computed on, up to the
+    # rounding of the host's LAPACK (through 28 truncated gate groups it moves log f by
+    # ~3e-7 between x86-64 and aarch64 builds; conditionals move far less than the bar)
+    assert abs(t.log_fidelity - float(gold["log_fidelity"])) < 1e-5
     path = str(tmp_path_factory.mktemp("cfg2") / "cfg2.tnsf")
     fixture.save(t, path)
     st = pkg.TNSState.load_file(path)

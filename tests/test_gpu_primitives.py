@@ -219,3 +219,25 @@ def test_device_contraction_planner(env, case):
         C = _contract(env, mode, la, A, sa, da, ca, lb, B, sb, db, cb, lc, dc)
         tol = (1e-13 if mode == 2 else (2 * K + 2) * 2.0 ** -23 + (6 * 2.0 ** -22 if mode == 1 else 0)) * ref_abs
         assert np.all(np.abs(C - ref) <= tol), (mode, np.max(np.abs(C - ref) / ref_abs))
+
+
+def test_tile_widths_are_bit_identical(env):
+    """Both tensor-core tile widths (128 and 256 real columns) give the same bits, so
+    the library's timing-based choice between them never changes a result."""
+    import ctypes as C
+    torch, lib = env
+    rng = np.random.default_rng(21)
+    for M, N, K in ((700, 200, 96), (4096, 96, 1024)):
+        A = (rng.normal(size=(M, K)) + 1j * rng.normal(size=(M, K))).astype(np.complex64)
+        B = (rng.normal(size=(N, K)) + 1j * rng.normal(size=(N, K))).astype(np.complex64)
+        dA = torch.tensor(A.view(np.float32), device="cuda")
+        dB = torch.tensor(B.view(np.float32), device="cuda")
+        out = []
+        for bn in (128, 256):
+            assert lib.tns_test_tc_tile(bn) == 0
+            dC = torch.full((M, 2 * N), float("nan"), device="cuda")
+            assert lib.tns_test_tcgemm(M, N, K, C.c_void_p(dA.data_ptr()), C.c_void_p(dB.data_ptr()),
+                                       C.c_void_p(dC.data_ptr()), None) == 0
+            out.append(dC.cpu())
+        assert lib.tns_test_tc_tile(0) == 0
+        assert torch.equal(out[0], out[1])
