@@ -32,7 +32,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "samples/s at <=1e-3 marginal error vs plain sampler; boundary-MPS TFLOP/s"
 CONFIG = "sq10x10"
-WORKLOAD = "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64"
+WORKLOADS = {
+    "sq10x10": "square 10x10 domain-wall Heisenberg quench, 7 layers dt=0.2, chi=16, chi_b=64",
+    "sq4x4": "square 4x4 domain-wall Heisenberg quench, 4 layers dt=0.2, chi=4, chi_b=16",
+    "heavyhex164": "heavy-hex 164 qubits (6x12 brick-wall honeycomb with bridges, degrees 2/3) domain-wall "
+                   "Heisenberg quench, 20 layers dt=0.2, chi=32, chi_b=128",
+    "ladder52": "2x26 ladder LUCJ-like circuit (Givens networks, phases, rung controlled phases; 3 repetitions), "
+                "chi=64, chi_b=256",
+}
+WORKLOAD = WORKLOADS[CONFIG]
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s SIMT FP32
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tf32 : bf16 tensor throughput
@@ -60,8 +68,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=None, help="samples per step (default 128; 1024 at 4x4)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default=CONFIG, choices=sorted(WORKLOADS),
+                    help="workload (the 10x10 square lattice is the headline; the others are the other paper shapes)")
     ap.add_argument("--mode", default="plain", choices=["plain", "learned"],
                     help="plain: the boundary-MPS sampler; learned: MADE proposal + independent MH on the same state")
     ap.add_argument("--train-samples", type=int, default=32768)
@@ -73,7 +83,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compression", default=None, metavar="P,Q,QENV",
                     help="range-finder oversampling, subspace iterations, environment iterations (library defaults)")
-    ap.add_argument("--plain-samples", type=int, default=8,
+    ap.add_argument("--plain-samples", type=int, default=4,
                     help="samples the plain FP64 sampler replays for its rate and the marginal error (0 = skip)")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--gemm-case", default=None, metavar="M,N,K",
@@ -112,12 +122,16 @@ def dist_env():
     return rank, world, local
 
 
-def workload():
+def workload(name: str | None = None):
+    """(config dict, lattice, initial bits, gate groups) of a named workload."""
     import workloads as w
-    cfg = w.CONFIGS[CONFIG]
+    cfg = w.CONFIGS[name or CONFIG]
     lat = w.make_lattice(cfg["lattice"])
-    bits = w.domain_wall_bits(lat)
-    groups = w.heisenberg_circuit(lat, cfg["layers"], cfg["dt"])
+    if "reps" in cfg:
+        groups, bits = w.lucj_like_circuit(lat, reps=cfg["reps"], seed=11424)
+    else:
+        bits = w.domain_wall_bits(lat)
+        groups = w.heisenberg_circuit(lat, cfg["layers"], cfg["dt"])
     return cfg, lat, bits, groups
 
 
@@ -592,7 +606,11 @@ def run_gemm_case(args):
 
 
 def main():
+    global CONFIG, WORKLOAD
     args = parse()
+    CONFIG, WORKLOAD = args.config, WORKLOADS[args.config]
+    if args.batch is None:
+        args.batch = 1024 if args.config == "sq4x4" else 128
     if args.gemm_case:
         run_gemm_case(args)
         return

@@ -141,6 +141,21 @@ tns_status tns_sample_replay(tns_state* s, int32_t chi_b, int64_t n, uint64_t se
 tns_status tns_amplitude(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev, double* log_abs_dev,
                          double* phase_dev);
 
+/*
+ * tns_certify -- check sampled bitstrings against an independent contraction
+ * (Methods, p(x) = |<x|psi>|^2 / <psi|psi>; Appendix, verification of the samples):
+ * log p(x) from tns_amplitude and tns_log_norm at rank chi_b (e.g. twice the
+ * sampling rank), and the statistics of w = p(x) / q(x) over the samples, which
+ * average to 1 when q is the sampling distribution (importance-sampling identity).
+ *   bits_dev    device uint8 [n][n_sites];  logq_dev  device float64 [n] (log q(x))
+ *   logp_dev    device float64 [n]: log p(x) (-inf for an exact zero)
+ *   stats_host  host float64 [5]: mean w, its standard error, mean(log q - log p)
+ *               (the KL-divergence estimate of q from p), samples with p > 0, and
+ *               log <psi|psi> at chi_b
+ */
+tns_status tns_certify(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev, const double* logq_dev,
+                       double* logp_dev, double* stats_host);
+
 /* Sum over applied two-qubit gates of log(1 - eps_i): log of the fidelity
  * estimate f of Eq. 2. */
 tns_status tns_log_fidelity(const tns_state* s, double* log_f);

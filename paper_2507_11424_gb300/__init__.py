@@ -196,6 +196,16 @@ class TNSState:
                                          C.c_void_p(cnd.data_ptr())), "tns_sample_replay")
         return logq, cnd
 
+    def certify(self, chi_b: int, bits, logq):
+        """(log p [n] device tensor, dict of p/q statistics) at certification rank chi_b (tns_certify)."""
+        torch = _torch()
+        n = bits.shape[0]
+        logp = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = np.zeros(5, dtype=np.float64)
+        check(self.lib.tns_certify(self._h, int(chi_b), int(n), C.c_void_p(bits.data_ptr()),
+                                   C.c_void_p(logq.data_ptr()), C.c_void_p(logp.data_ptr()), _ptr(st)), "tns_certify")
+        return logp, dict(mean_ratio=st[0], mean_ratio_se=st[1], kld=st[2], n_finite=int(st[3]), log_norm=st[4])
+
     def amplitude(self, chi_b: int, bits):
         torch = _torch()
         n = bits.shape[0]

@@ -35,6 +35,7 @@ SIGNATURES = {
     "tns_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),
     "tns_set_compression": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "tns_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "tns_certify": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_test_tc_tile": (C.c_int, [C.c_int32]),
     "tns_direct_marginals": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "tns_query": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),

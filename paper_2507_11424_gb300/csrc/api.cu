@@ -140,6 +140,9 @@ static void free_state(tns_state* s) {
   for (auto& g : s->graphs)
     if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
   s->graphs.clear();
+  for (auto& e : s->gev)
+    if (e) cudaEventDestroy(e);
+  if (s->gstream) cudaStreamDestroy(s->gstream);
   for (auto* ec : {&s->env, &s->env_top})
     for (auto& E : ec->E)
       for (auto p : E.site)
@@ -302,6 +305,15 @@ extern "C" tns_status tns_amplitude(tns_state* s, int32_t chi_b, int64_t n, cons
     return TNS_ERR_ARG;
   }
   return amplitude(s, chi_b, n, bits_dev, log_abs_dev, phase_dev);
+}
+
+extern "C" tns_status tns_certify(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev,
+                                  const double* logq_dev, double* logp_dev, double* stats_host) {
+  if (!s || chi_b < 1 || n < 0 || !stats_host || (n > 0 && (!bits_dev || !logq_dev || !logp_dev))) {
+    set_error("invalid argument to tns_certify");
+    return TNS_ERR_ARG;
+  }
+  return certify(s, chi_b, n, bits_dev, logq_dev, logp_dev, stats_host);
 }
 
 extern "C" tns_status tns_log_fidelity(const tns_state* s, double* log_f) {

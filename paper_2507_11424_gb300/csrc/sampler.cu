@@ -328,14 +328,21 @@ __global__ void transpose_conj_kernel(const C* __restrict__ T, C* __restrict__ T
 // streams through shared memory 32 rows at a time.  gram_reduce_kernel adds the
 // splits in index order (deterministic).
 constexpr int GRAM_MAX_N = 128;
-__global__ void gram_partial_kernel(const cf* __restrict__ Y, long long M, int n, long long rows_per,
-                                    cf* __restrict__ P) {
+// G is Hermitian: block (split, b) computes only the 4 x 4 tiles on and above the
+// diagonal, one tile per thread (threadIdx.x enumerates them row by row), and the
+// reduction fills the lower triangle by conjugation.
+__global__ void __launch_bounds__(528) gram_partial_kernel(const cf* __restrict__ Y, long long M, int n,
+                                                            long long rows_per, cf* __restrict__ P) {
   __shared__ cf ys[32][GRAM_MAX_N];
   const long long b = blockIdx.y;
   const int split = blockIdx.x;
   const long long r0 = split * rows_per, r1 = min(M, r0 + rows_per);
   const cf* src = Y + b * M * n;
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int nb = (n + 3) / 4;
+  int ty = 0, tx = threadIdx.x;                 // upper-triangular tile (ty <= tx)
+  while (ty < nb && tx >= nb - ty) { tx -= nb - ty; ++ty; }
+  tx += ty;
+  const bool active = ty < nb;
   float2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -343,27 +350,32 @@ __global__ void gram_partial_kernel(const cf* __restrict__ Y, long long M, int n
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   for (long long m0 = r0; m0 < r1; m0 += 32) {
     const int rows = (int)(r1 - m0 < 32 ? r1 - m0 : 32);
-    for (int r = ty; r < 32; r += blockDim.y)
-      for (int c = tx; c < n; c += blockDim.x) ys[r][c] = r < rows ? src[(m0 + r) * n + c] : make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < 32 * n; e += blockDim.x) {
+      const int r = e / n, c = e % n;
+      ys[r][c] = r < rows ? src[(m0 + r) * n + c] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    for (int r = 0; r < rows; ++r) {
-      float2 a[4], v[4];
+    if (active) {
+      for (int r = 0; r < rows; ++r) {
+        float2 a[4], v[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int ci = 4 * ty + i, cj = 4 * tx + i;
-        a[i] = ci < n ? ys[r][ci] : make_float2(0.f, 0.f);
-        v[i] = cj < n ? ys[r][cj] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {          // acc += conj(a_i) v_j
-          acc[i][j].x = fmaf(a[i].x, v[j].x, fmaf(a[i].y, v[j].y, acc[i][j].x));
-          acc[i][j].y = fmaf(a[i].x, v[j].y, fmaf(-a[i].y, v[j].x, acc[i][j].y));
+        for (int i = 0; i < 4; ++i) {
+          const int ci = 4 * ty + i, cj = 4 * tx + i;
+          a[i] = ci < n ? ys[r][ci] : make_float2(0.f, 0.f);
+          v[i] = cj < n ? ys[r][cj] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {          // acc += conj(a_i) v_j
+            acc[i][j].x = fmaf(a[i].x, v[j].x, fmaf(a[i].y, v[j].y, acc[i][j].x));
+            acc[i][j].y = fmaf(a[i].x, v[j].y, fmaf(-a[i].y, v[j].x, acc[i][j].y));
+          }
+      }
     }
     __syncthreads();
   }
+  if (!active) return;
   cf* dst = P + (b * gridDim.x + split) * (long long)n * n;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -374,16 +386,22 @@ __global__ void gram_partial_kernel(const cf* __restrict__ Y, long long M, int n
     }
 }
 
-__global__ void gram_reduce_kernel(const cf* __restrict__ P, int splits, long long nn, long long total,
-                                   cf* __restrict__ G) {
+// G[b][i][j] = sum of the splits' partial Grams in index order, read from the computed
+// upper triangle of 4 x 4 tiles (conjugated for entries below it).
+__global__ void gram_reduce_kernel(const cf* __restrict__ P, int splits, int n, long long total, cf* __restrict__ G) {
+  const long long nn = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / nn, e = i % nn;
+    const int r = (int)(e / n), c = (int)(e % n);
+    const bool upper = (r / 4) <= (c / 4);
+    const long long src = upper ? e : (long long)c * n + r;
     float2 acc = make_float2(0.f, 0.f);
     for (int k = 0; k < splits; ++k) {
-      const float2 v = P[(b * splits + k) * nn + e];
+      const float2 v = P[(b * splits + k) * nn + src];
       acc.x += v.x;
       acc.y += v.y;
     }
+    if (!upper) acc.y = -acc.y;
     G[i] = acc;
   }
 }
@@ -425,23 +443,19 @@ static cudaError_t pgram(tns_state* s, Prec p, const void* Y, long long S, long 
   const long long rows_per = (M + splits - 1) / splits;
   splits = (int)((M + rows_per - 1) / rows_per);
   cudaEvent_t ev = s->prof.begin(s->st);
-  cf* P = (cf*)G;
-  if (splits > 1) {
-    cudaError_t e = cudaMallocAsync((void**)&P, sizeof(cf) * (size_t)S * splits * n * n, s->st);
-    if (e != cudaSuccess) return e;
-  }
+  cf* P = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&P, sizeof(cf) * (size_t)S * splits * n * n, s->st);
+  if (e != cudaSuccess) return e;
   const int nb = (n + 3) / 4;
-  gram_partial_kernel<<<dim3((unsigned)splits, (unsigned)S), dim3(nb, nb), 0, s->st>>>((const cf*)Y, M, n, rows_per, P);
+  gram_partial_kernel<<<dim3((unsigned)splits, (unsigned)S), nb * (nb + 1) / 2, 0, s->st>>>((const cf*)Y, M, n,
+                                                                                           rows_per, P);
   s->launches++;
-  cudaError_t e = cudaGetLastError();
-  if (splits > 1) {
-    const long long total = S * (long long)n * n;
-    if (e == cudaSuccess)
-      gram_reduce_kernel<<<nblk(total), 256, 0, s->st>>>(P, splits, (long long)n * n, total, (cf*)G);
-    s->launches++;
-    if (e == cudaSuccess) e = cudaGetLastError();
-    cudaFreeAsync(P, s->st);
-  }
+  e = cudaGetLastError();
+  const long long total = S * (long long)n * n;
+  if (e == cudaSuccess) gram_reduce_kernel<<<nblk(total), 256, 0, s->st>>>(P, splits, n, total, (cf*)G);
+  s->launches++;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaFreeAsync(P, s->st);
   s->prof.end(PC_ZIP_SIMT, ev, 8.0 * (double)S * M * n * n, s->st);
   return e;
 }
@@ -1163,25 +1177,40 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
     const std::vector<long long> key = {s->version, R, S, cx.f64 ? 1 : 0, (long long)cx.gp, cx.p, cx.q,
                                         s->tensor_cores ? 1 : 0, s->ws.gen, s->env_builds, s->work_gen};
     auto it = s->graphs.find(key);
+    if (it == s->graphs.end() && !s->graph_seen.count(key)) {   // first time: run eagerly (sizes every buffer)
+      s->graph_seen.insert(key);
+      TNS_TRY(run_chunk(S));
+      continue;
+    }
+    // Graphs are captured and replayed on a private stream (the caller's may be the legacy
+    // default stream, which cannot be captured), ordered after and before the caller's
+    // stream by events.
+    if (!s->gstream) {
+      TNS_TRY_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+      for (auto& e : s->gev) TNS_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t caller = s->st;
+    TNS_TRY_CUDA(cudaEventRecord(s->gev[0], caller));
+    TNS_TRY_CUDA(cudaStreamWaitEvent(s->gstream, s->gev[0], 0));
     if (it == s->graphs.end()) {
-      if (!s->graph_seen.count(key)) {            // first time: run eagerly (sizes every buffer)
-        s->graph_seen.insert(key);
-        TNS_TRY(run_chunk(S));
-        continue;
-      }
-      const long long l0 = s->launches;
-      TNS_TRY_CUDA(cudaStreamBeginCapture(cx.st, cudaStreamCaptureModeThreadLocal));
-      tns_status rs = run_chunk(S);
+      const long long l0 = s->launches, c0 = contract_launches();
+      s->st = cx.st = s->gstream;
+      cudaError_t eb = cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal);
+      tns_status rs = eb == cudaSuccess ? run_chunk(S) : TNS_OK;
       cudaGraph_t g = nullptr;
-      cudaError_t ec = cudaStreamEndCapture(cx.st, &g);
+      cudaError_t ec = eb == cudaSuccess ? cudaStreamEndCapture(s->gstream, &g) : eb;
+      s->st = cx.st = caller;
       if (rs != TNS_OK) {
         if (g) cudaGraphDestroy(g);
         return rs;
       }
       TNS_TRY_CUDA(ec);
+      // kernels recorded during capture were counted but not launched; the graph's
+      // launches are counted on every replay instead
       tns_state::GraphEntry en;
-      en.launches = s->launches - l0;
-      s->launches = l0;
+      const long long cdelta = contract_launches() - c0;
+      en.launches = (s->launches - l0) + cdelta;
+      s->launches = l0 - cdelta;
       ec = cudaGraphInstantiate(&en.exec, g, 0);
       cudaGraphDestroy(g);
       TNS_TRY_CUDA(ec);
@@ -1192,8 +1221,10 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
       }
       it = s->graphs.emplace(key, en).first;
     }
-    TNS_TRY_CUDA(cudaGraphLaunch(it->second.exec, cx.st));
+    TNS_TRY_CUDA(cudaGraphLaunch(it->second.exec, s->gstream));
     s->launches += it->second.launches;
+    TNS_TRY_CUDA(cudaEventRecord(s->gev[1], s->gstream));
+    TNS_TRY_CUDA(cudaStreamWaitEvent(caller, s->gev[1], 0));
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
   s->prof.resolve();
@@ -1531,5 +1562,60 @@ tns_status direct_marginals(tns_state* s, int chi_b, double* one, double* two) {
   }
   TNS_TRY_CUDA(cudaStreamSynchronize(cx.st));
   return check_tc_error(cx);
+}
+
+// ------------------------------------------------------- sample certification
+// log p(x) = 2 log|<x|psi>| - log <psi|psi> at the certification rank; the ratio
+// w = p / q and the per-sample log q - log p, reduced (one block, fixed order) to
+// sum w, sum w^2, sum (log q - log p) and the number of samples with p > 0.
+__global__ void __launch_bounds__(1024) certify_kernel(const double* log_abs, double log_norm, const double* logq,
+                                                       long long n, double* logp, double* stats) {
+  __shared__ double r0[1024], r1[1024], r2[1024], r3[1024];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double lp = 2.0 * log_abs[i] - log_norm;
+    logp[i] = lp;
+    if (isfinite(lp)) {
+      const double w = exp(lp - logq[i]);
+      s0 += w;
+      s1 += w * w;
+      s2 += logq[i] - lp;
+      s3 += 1.0;
+    }
+  }
+  r0[threadIdx.x] = s0; r1[threadIdx.x] = s1; r2[threadIdx.x] = s2; r3[threadIdx.x] = s3;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      r0[threadIdx.x] += r0[threadIdx.x + o]; r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o]; r3[threadIdx.x] += r3[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { stats[0] = r0[0]; stats[1] = r1[0]; stats[2] = r2[0]; stats[3] = r3[0]; }
+}
+
+tns_status certify(tns_state* s, int chi_b, long long n, const uint8_t* bits, const double* logq, double* logp,
+                   double* stats_host) {
+  double ln = 0.0;
+  TNS_TRY(log_norm(s, chi_b, &ln));
+  double *la, *ph, *st;
+  TNS_TRY(wsget(s, "c_la", sizeof(double) * std::max<long long>(n, 1), (void**)&la));
+  TNS_TRY(wsget(s, "c_ph", sizeof(double) * std::max<long long>(n, 1), (void**)&ph));
+  TNS_TRY(wsget(s, "c_stats", sizeof(double) * 4, (void**)&st));
+  TNS_TRY(amplitude(s, chi_b, n, bits, la, ph));
+  certify_kernel<<<1, 1024, 0, s->st>>>(la, ln, logq, n, logp, st);
+  s->launches++;
+  TNS_TRY_CUDA(cudaGetLastError());
+  double h[4];
+  TNS_TRY_CUDA(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, s->st));
+  TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
+  const double m = h[3] > 0 ? h[3] : 1.0;
+  stats_host[0] = h[0] / m;                                                   // mean p/q
+  stats_host[1] = h[3] > 1 ? std::sqrt(std::max(0.0, h[1] / m - stats_host[0] * stats_host[0]) / (m - 1)) : NAN;
+  stats_host[2] = h[2] / m;                                                   // KLD estimate
+  stats_host[3] = h[3];
+  stats_host[4] = ln;
+  return TNS_OK;
 }
 }  // namespace tns

@@ -109,6 +109,8 @@ struct tns_state {
   long long env_builds = 0;             // bumped when norm environments are rebuilt
   long long work_gen = 0;               // bumped when the working-precision cell copies change
   unsigned char host_call[64] = {};     // staging for the per-call parameter block
+  cudaStream_t gstream = nullptr;       // private stream that graphs are captured and replayed on
+  cudaEvent_t gev[2] = {nullptr, nullptr};
   long long work_version = -1;
 
   int cidx(int r, int c) const { return r * W + c; }
@@ -143,4 +145,6 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
 tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase);
 tns_status log_norm(tns_state* s, int chi_b, double* out);
 tns_status direct_marginals(tns_state* s, int chi_b, double* one, double* two);
+tns_status certify(tns_state* s, int chi_b, long long n, const uint8_t* bits, const double* logq, double* logp,
+                   double* stats_host);
 }  // namespace tns

@@ -96,3 +96,31 @@ def test_direct_marginals_match_oracle(pkg, tmp_path, H, W, L, chi, R, kind, pre
     assert np.array_equal(mask, ~np.isnan(two))
     assert np.abs(two[mask] - two_o[mask]).max() < tol
     st.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_certification_matches_oracle(pkg, tmp_path, prec, tol):
+    """tns_certify against oracle/bmps.certify: the oracle draws 24 samples at rank 8
+    from its own 4x4 state (chi = 4, 4 layers); both certify them at rank 16 (log p,
+    mean p/q, KL estimate).  The oracle's bits and log q are the input to both."""
+    import torch
+    from oracle import bmps
+    lat = w.square(4, 4)
+    bits0 = w.domain_wall_bits(lat)
+    t = GridTNS(lat.grid_rc, lat.edges, bits0)
+    for g in w.heisenberg_circuit(lat, 4, 0.2):
+        t.apply_group(g, 4)
+        t.bp(500, 1e-12)
+    xs, logq, _ = bmps.sample(t, 8, 24, seed=31)
+    ref = bmps.certify(t, xs, logq, 16)
+    path = str(tmp_path / "cert.tnsf")
+    fixture.save(t, path)
+    st = pkg.TNSState.load_file(path)
+    st.n = t.n
+    st.set_precision(prec)
+    logp, stats = st.certify(16, torch.tensor(xs, device="cuda"), torch.tensor(logq, device="cuda"))
+    assert np.abs(logp.cpu().numpy() - ref["log_p"]).max() < tol * 10
+    assert abs(stats["mean_ratio"] - ref["mean_ratio"]) < tol * 10
+    assert abs(stats["kld"] - ref["kld"]) < tol * 10
+    assert stats["n_finite"] == 24
+    st.close()
