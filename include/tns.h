@@ -124,6 +124,17 @@ tns_status tns_sample(tns_state* s, int32_t chi_b, int64_t n_samples, uint64_t s
                       double* logq_dev, double* cond_dev);
 
 /*
+ * tns_sample_range -- samples first .. first + n_samples - 1 of the stream that
+ * tns_sample draws for this (state, chi_b, seed): output row r holds sample
+ * first + r (Philox counter (first + r, q)), bit-identical to row first + r of a
+ * tns_sample call with at least first + n_samples samples.  Samples are
+ * independent draws, so disjoint ranges shard one stream across devices or calls
+ * with no exchange between them.  first < 0 is TNS_ERR_ARG; buffers as tns_sample.
+ */
+tns_status tns_sample_range(tns_state* s, int32_t chi_b, int64_t first, int64_t n_samples, uint64_t seed,
+                            uint8_t* bits_dev, double* logq_dev, double* cond_dev);
+
+/*
  * tns_sample_replay -- like tns_sample, but the bits are given (bits_dev is read,
  * not written) and only the conditionals and log q along them are computed
  * (forced-path replay; used to verify samples and to score bitstrings under q).
@@ -272,10 +283,23 @@ tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_m
  * or threads using one device) race: order them on one stream.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
- * Convergence is not reported (no host synchronisation).
+ * Convergence is not reported by this call (no host synchronisation): the
+ * per-matrix status words stay in the scratch for tns_eigh_noalloc_status.
  */
 tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A_dev, double* lam_dev, double* V_dev,
                             void* cuda_stream);
+
+/*
+ * tns_eigh_noalloc_status -- the convergence status of the last tns_eigh_noalloc
+ * call on the current device, as a stream-ordered device-to-device copy (no
+ * allocation, no host wait): status_dev (device int32 [batch], caller-owned)
+ * receives, per matrix, 0 if the Jacobi sweeps converged and 1 if they stopped at
+ * the sweep cap (the condition the allocating entry points return as
+ * TNS_ERR_NUMERIC).  Issue it on the stream of that call and before the next one;
+ * batch above the last call's batch returns TNS_ERR_ARG.  The paper has no
+ * counterpart.
+ */
+tns_status tns_eigh_noalloc_status(int32_t batch, int32_t* status_dev, void* cuda_stream);
 
 /*
  * Learned proposal and independent Metropolis-Hastings.  The paper samples only

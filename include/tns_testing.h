@@ -86,6 +86,16 @@ tns_status tns_test_plan(const char* labels_a, const int64_t* dims_a, const int6
 tns_status tns_test_svd(int32_t batch, int32_t m, int32_t n, const double* A_dev, double* s_dev, double* U_dev,
                         double* V_dev, void* cuda_stream);
 
+/* One site of a cached bottom norm environment E[b] (built by the last tns_log_norm
+ * or tns_sample call), in its stored form: dims_out (host int64 [4]) receives its
+ * left bond, its two physical dims and its right bond in storage order;
+ * reversed_out (host, may be NULL) whether the environment is stored in reversed
+ * column order (stored site k is column W-1-k with bonds swapped); out_host (host
+ * complex128, row-major, may be NULL to query dims) the entries, widened from the
+ * working precision.  TNS_ERR_STATE when no environment is cached. */
+tns_status tns_test_env_site(tns_state* s, int32_t b, int32_t k, int64_t* dims_out, int32_t* reversed_out,
+                             double* out_host);
+
 #ifdef __cplusplus
 }
 #endif

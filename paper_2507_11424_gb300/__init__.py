@@ -171,8 +171,10 @@ class TNSState:
         return out
 
     # ---------------------------------------------------------------- sampling
-    def sample(self, chi_b: int, n: int, seed: int, n_sites: int | None = None, cond: bool = False, out=None):
-        """Draw n samples; returns torch CUDA tensors (bits uint8 [n, n_sites], logq f64 [n][, cond])."""
+    def sample(self, chi_b: int, n: int, seed: int, n_sites: int | None = None, cond: bool = False, out=None,
+               first: int = 0):
+        """Draw n samples; returns torch CUDA tensors (bits uint8 [n, n_sites], logq f64 [n][, cond]).
+        first > 0 draws samples first .. first + n - 1 of the seed's stream (tns_sample_range)."""
         torch = _torch()
         ns = n_sites or self.n
         if out is None:
@@ -181,9 +183,13 @@ class TNSState:
             cnd = torch.zeros((n, ns), dtype=torch.float64, device="cuda") if cond else None
         else:
             bits, logq, cnd = out
-        check(self.lib.tns_sample(self._h, int(chi_b), int(n), C.c_uint64(int(seed) & (2**64 - 1)),
-                                  C.c_void_p(bits.data_ptr()), C.c_void_p(logq.data_ptr()),
-                                  C.c_void_p(cnd.data_ptr()) if cnd is not None else None), "tns_sample")
+        ptrs = (C.c_void_p(bits.data_ptr()), C.c_void_p(logq.data_ptr()),
+                C.c_void_p(cnd.data_ptr()) if cnd is not None else None)
+        sd = C.c_uint64(int(seed) & (2**64 - 1))
+        if first:
+            check(self.lib.tns_sample_range(self._h, int(chi_b), int(first), int(n), sd, *ptrs), "tns_sample_range")
+        else:
+            check(self.lib.tns_sample(self._h, int(chi_b), int(n), sd, *ptrs), "tns_sample")
         return (bits, logq, cnd) if cond else (bits, logq)
 
     def sample_replay(self, chi_b: int, bits, seed: int = 0):

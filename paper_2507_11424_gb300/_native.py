@@ -26,6 +26,8 @@ SIGNATURES = {
                                        C.c_void_p]),
     "tns_bp_gauge": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "tns_sample": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tns_sample_range": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
     "tns_sample_replay": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "tns_amplitude": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -47,6 +49,8 @@ SIGNATURES = {
     "tns_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double)]),
     "tns_eigh_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tns_eigh_noalloc_status": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
+    "tns_test_env_site": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_made_create": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "tns_made_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "tns_made_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_float,

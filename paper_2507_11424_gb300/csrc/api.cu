@@ -261,6 +261,7 @@ extern "C" void tns_destroy(tns_state* s) {
 
 extern "C" tns_status tns_apply_gate_layer(tns_state* s, int32_t n_gates, const int32_t* sites, const double* mats,
                                            int32_t chi, double svd_cutoff, double* eps_out) {
+  LaunchScope ls_(s);
   if (!s || n_gates < 0 || (n_gates > 0 && (!sites || !mats)) || chi < 1 || chi > s->chi_max ||
       !(svd_cutoff >= 0.0)) {
     set_error("invalid argument to tns_apply_gate_layer");
@@ -271,6 +272,7 @@ extern "C" tns_status tns_apply_gate_layer(tns_state* s, int32_t n_gates, const 
 
 extern "C" tns_status tns_bp_gauge(tns_state* s, int32_t max_iter, double tol, int32_t* iters_out,
                                    double* residual_out) {
+  LaunchScope ls_(s);
   if (!s || max_iter < 1 || !(tol >= 0.0)) { set_error("invalid argument to tns_bp_gauge"); return TNS_ERR_ARG; }
   int it = 0;
   double res = 0.0;
@@ -282,6 +284,7 @@ extern "C" tns_status tns_bp_gauge(tns_state* s, int32_t max_iter, double tol, i
 
 extern "C" tns_status tns_sample(tns_state* s, int32_t chi_b, int64_t n_samples, uint64_t seed, uint8_t* bits_dev,
                                  double* logq_dev, double* cond_dev) {
+  LaunchScope ls_(s);
   if (!s || chi_b < 1 || n_samples < 0 || (n_samples > 0 && (!bits_dev || !logq_dev))) {
     set_error("invalid argument to tns_sample");
     return TNS_ERR_ARG;
@@ -289,8 +292,19 @@ extern "C" tns_status tns_sample(tns_state* s, int32_t chi_b, int64_t n_samples,
   return sample(s, chi_b, n_samples, seed, nullptr, bits_dev, logq_dev, cond_dev);
 }
 
+extern "C" tns_status tns_sample_range(tns_state* s, int32_t chi_b, int64_t first, int64_t n_samples, uint64_t seed,
+                                       uint8_t* bits_dev, double* logq_dev, double* cond_dev) {
+  LaunchScope ls_(s);
+  if (!s || chi_b < 1 || first < 0 || n_samples < 0 || (n_samples > 0 && (!bits_dev || !logq_dev))) {
+    set_error("invalid argument to tns_sample_range");
+    return TNS_ERR_ARG;
+  }
+  return sample(s, chi_b, n_samples, seed, nullptr, bits_dev, logq_dev, cond_dev, first);
+}
+
 extern "C" tns_status tns_sample_replay(tns_state* s, int32_t chi_b, int64_t n, uint64_t seed,
                                         const uint8_t* bits_dev, double* logq_dev, double* cond_dev) {
+  LaunchScope ls_(s);
   if (!s || chi_b < 1 || n < 0 || (n > 0 && (!bits_dev || !logq_dev))) {
     set_error("invalid argument to tns_sample_replay");
     return TNS_ERR_ARG;
@@ -300,6 +314,7 @@ extern "C" tns_status tns_sample_replay(tns_state* s, int32_t chi_b, int64_t n, 
 
 extern "C" tns_status tns_amplitude(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev,
                                     double* log_abs_dev, double* phase_dev) {
+  LaunchScope ls_(s);
   if (!s || chi_b < 1 || n < 0 || (n > 0 && (!bits_dev || !log_abs_dev || !phase_dev))) {
     set_error("invalid argument to tns_amplitude");
     return TNS_ERR_ARG;
@@ -309,6 +324,7 @@ extern "C" tns_status tns_amplitude(tns_state* s, int32_t chi_b, int64_t n, cons
 
 extern "C" tns_status tns_certify(tns_state* s, int32_t chi_b, int64_t n, const uint8_t* bits_dev,
                                   const double* logq_dev, double* logp_dev, double* stats_host) {
+  LaunchScope ls_(s);
   if (!s || chi_b < 1 || n < 0 || !stats_host || (n > 0 && (!bits_dev || !logq_dev || !logp_dev))) {
     set_error("invalid argument to tns_certify");
     return TNS_ERR_ARG;
@@ -323,16 +339,19 @@ extern "C" tns_status tns_log_fidelity(const tns_state* s, double* log_f) {
 }
 
 extern "C" tns_status tns_log_norm(tns_state* s, int32_t chi_b, double* out) {
+  LaunchScope ls_(s);
   if (!s || !out || chi_b < 1) { set_error("invalid argument to tns_log_norm"); return TNS_ERR_ARG; }
   return log_norm(s, chi_b, out);
 }
 
 extern "C" tns_status tns_direct_marginals(tns_state* s, int32_t chi_b, double* one_host, double* two_host) {
+  LaunchScope ls_(s);
   if (!s || !one_host || chi_b < 1) { set_error("invalid argument to tns_direct_marginals"); return TNS_ERR_ARG; }
   return direct_marginals(s, chi_b, one_host, two_host);
 }
 
 extern "C" tns_status tns_set_precision(tns_state* s, tns_prec prec) {
+  LaunchScope ls_(s);
   if (!s || (prec != TNS_PREC_FP64 && prec != TNS_PREC_MIXED)) { set_error("invalid precision"); return TNS_ERR_ARG; }
   s->prec = prec;
   return TNS_OK;
@@ -377,7 +396,7 @@ extern "C" tns_status tns_query(const tns_state* s, int32_t* H, int32_t* W, int3
 
 extern "C" tns_status tns_launch_count(const tns_state* s, int64_t* launches) {
   if (!s || !launches) { set_error("invalid argument"); return TNS_ERR_ARG; }
-  *launches = s->launches + contract_launches();
+  *launches = s->launches;
   return TNS_OK;
 }
 

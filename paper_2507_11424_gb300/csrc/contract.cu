@@ -8,8 +8,10 @@
 
 namespace tns {
 
-static std::atomic<long long> g_launches{0};
-long long contract_launches() { return g_launches.load(); }
+// Launches of this thread's contractions (the API entry points attribute the
+// difference across a call to the state they run on).
+static thread_local long long g_launches = 0;
+long long contract_launches() { return g_launches; }
 
 TView view(void* p, const std::string& labels, const std::vector<long long>& dims, bool conj) {
   TView v;

@@ -14,6 +14,8 @@ static constexpr int JAC_THREADS = 256;
 static constexpr int EIG_THREADS = 1024;
 static constexpr int MAX_SWEEPS = 40;
 static constexpr size_t SMEM_LIMIT = 200 * 1024;
+// Largest Cholesky order (the in-place inverse stages one column of n entries).
+static constexpr int CHOL_MAX_N = 512;
 
 bool jacobi_fits_smem(int m, int n) {
   size_t np = n + (n & 1);
@@ -78,17 +80,20 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
   const int b = blockIdx.x, tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   const int np = n + (n & 1), half = np / 2;
+  // row pitch: np + 1 in shared memory (odd, so the column phase's strided walks are
+  // free of bank conflicts), np in global memory
+  const int ld = use_smem ? np + 1 : np;
   C* a = use_smem ? reinterpret_cast<C*>(smraw4) : work + (long long)b * 2 * np * np;
-  C* v = a + (long long)np * np;
+  C* v = a + (long long)np * ld;
   const C* src = Ain + (long long)b * sA;
   T tot = 0;
   for (int idx = tid; idx < np * np; idx += blockDim.x) {
     int i = idx / np, j = idx % np;
     C x = (i < n && j < n) ? src[(long long)i * lda + j] : mk((T)0, (T)0);
     if (i == j) x.y = 0;            // Hermitian: real diagonal
-    a[idx] = x;
+    a[i * ld + j] = x;
     tot += cabs2(x);
-    v[idx] = mk(i == j ? (T)1 : (T)0, (T)0);
+    v[i * ld + j] = mk(i == j ? (T)1 : (T)0, (T)0);
   }
   tot = warp_sum(tot);
   if ((tid & 31) == 0) red[tid >> 5] = tot;
@@ -111,8 +116,8 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
         rr_pair(r, i, np, p, q);
         cs_p[i] = p;
         cs_q[i] = q;
-        T app = a[p * np + p].x, aqq = a[q * np + q].x;
-        C apq = a[p * np + q];
+        T app = a[p * ld + p].x, aqq = a[q * ld + q].x;
+        C apq = a[p * ld + q];
         T ab = sqrt(cabs2(apq));
         T c = 1, s = 0, dl = 0;
         C e = mk((T)1, (T)0);
@@ -133,10 +138,10 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
         const T c = cs_c[i], s = cs_s[i];
         const C e = cs_e[i];
         for (int j = lane; j < np; j += 32) {
-          C ap = a[p * np + j], aq = a[q * np + j];
+          C ap = a[p * ld + j], aq = a[q * ld + j];
           C eaq = cmul(e, aq);
-          a[p * np + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-          a[q * np + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+          a[p * ld + j] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+          a[q * ld + j] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
         }
       }
       __syncthreads();
@@ -146,22 +151,22 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
         const T c = cs_c[i], s = cs_s[i];
         const C ec = cconj(cs_e[i]);
         for (int j = lane; j < np; j += 32) {
-          C ap = a[j * np + p], aq = a[j * np + q];
+          C ap = a[j * ld + p], aq = a[j * ld + q];
           C eaq = cmul(ec, aq);
-          a[j * np + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-          a[j * np + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
-          C vp = v[j * np + p], vq = v[j * np + q];
+          a[j * ld + p] = mk(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+          a[j * ld + q] = mk(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+          C vp = v[j * ld + p], vq = v[j * ld + q];
           C evq = cmul(ec, vq);
-          v[j * np + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
-          v[j * np + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
+          v[j * ld + p] = mk(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
+          v[j * ld + q] = mk(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
         }
       }
       __syncthreads();
       for (int i = tid; i < half; i += blockDim.x) {                   // exact 2x2 result
         if (cs_s[i] == 0) continue;
         const int p = cs_p[i], q = cs_q[i];
-        a[p * np + q] = mk((T)0, (T)0);
-        a[q * np + p] = mk((T)0, (T)0);
+        a[p * ld + q] = mk((T)0, (T)0);
+        a[q * ld + p] = mk((T)0, (T)0);
       }
       __syncthreads();
     }
@@ -171,15 +176,15 @@ eigh_kernel(const typename CplxOf<T>::type* Ain, long long sA, int lda, int n, d
   if (tid == 0 && status) status[b] = conv ? 0 : 1;
   if (tid == 0 && sweeps_out) sweeps_out[b] = sweeps_done;
   for (int i = tid; i < n; i += blockDim.x) {
-    T li = a[i * np + i].x;
+    T li = a[i * ld + i].x;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      T lj = a[j * np + j].x;
+      T lj = a[j * ld + j].x;
       if (lj > li || (lj == li && j < i)) ++rank;
     }
     lam[(long long)b * n + rank] = (double)li;
     cd* vo = Vout + (long long)b * sV;
-    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = to_cd(v[row * np + i]);
+    for (int row = 0; row < n; ++row) vo[(long long)row * n + rank] = to_cd(v[row * ld + i]);
   }
 }
 
@@ -292,12 +297,14 @@ svd_kernel(cd* Ain, long long sA, int lda, int m, int n, double* sigma, cd* Uout
 }
 
 // W = L^{-H} with L L^H = G + shift * max_i G_ii * I (G Hermitian PSD, n x n).
-// One block per matrix: right-looking Cholesky, then forward substitution for
-// the columns of L^{-1} (one thread per column).  Used so that Y W has
-// orthonormal columns when G = Y^H Y; the shift keeps it well defined for
+// One block per matrix, the factor held in one n x n buffer with row pitch n + 1
+// (an odd pitch keeps the column walks of both phases free of shared-memory bank
+// conflicts): right-looking Cholesky, then the triangular inverse in place
+// (columns from the last to the first: column j of L^{-1} is -L^{-1}[j+1:, j+1:]
+// L[j+1:, j] / L[j, j], from the already inverted trailing block).  Used so that
+// Y W has orthonormal columns when G = Y^H Y; the shift keeps it well defined for
 // rank-deficient Y and damps directions below shift * max G_ii smoothly.
-// use_smem: 2 = L and X = L^{-1} in shared memory, 1 = L in shared memory and X in
-// work (n^2 per matrix), 0 = both in work (2 n^2 per matrix).
+// use_smem: 1 = the buffer in shared memory, 0 = in work (n (n + 1) per matrix).
 template <typename C, typename GIN, typename T>
 __global__ void __launch_bounds__(JAC_THREADS)
 chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::type* work, int use_smem) {
@@ -305,17 +312,17 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
   extern __shared__ double4 smraw4[];
   __shared__ T red[JAC_THREADS / 32];
   __shared__ T sh_s;
+  __shared__ CT xs[CHOL_MAX_N];
   const int b = blockIdx.x, tid = threadIdx.x;
-  const long long nn = (long long)n * n;
-  CT* L = use_smem ? reinterpret_cast<CT*>(smraw4) : work + (long long)b * 2 * nn;
-  CT* X = use_smem == 2 ? L + nn : (use_smem == 1 ? work + (long long)b * nn : L + nn);
+  const int ld = n + 1;
+  CT* L = use_smem ? reinterpret_cast<CT*>(smraw4) : work + (long long)b * n * ld;
   const GIN* G = Gin + (long long)b * n * n;
   T mx = 0;
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     int i = idx / n, j = idx % n;
     const GIN gi = G[idx];
     CT g = mk((T)gi.x, (T)gi.y);
-    L[idx] = (j <= i) ? g : mk((T)0, (T)0);
+    L[i * ld + j] = (j <= i) ? g : mk((T)0, (T)0);
     if (i == j) mx = fmax(mx, g.x);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -333,7 +340,7 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
     for (int idx = tid; idx < n * n; idx += blockDim.x) W[idx] = from_cd<C>(mk(0.0, 0.0));
     return;
   }
-  for (int i = tid; i < n; i += blockDim.x) L[i * n + i].x += sft;
+  for (int i = tid; i < n; i += blockDim.x) L[i * ld + i].x += sft;
   __syncthreads();
   __shared__ int broke;
   for (int j = 0; j < n; ++j) {
@@ -343,36 +350,39 @@ chol_w_kernel(const GIN* Gin, int n, double shift, C* Wout, typename CplxOf<T>::
       // direction: the pivot is set to sqrt(sft) and the column decoupled from the
       // rest (zeroed below the diagonal), so the factor and its inverse stay bounded
       // by 1/sqrt(sft) instead of growing through the remaining columns.
-      T d = L[j * n + j].x;
+      T d = L[j * ld + j].x;
       broke = !(d > sft);
-      L[j * n + j] = mk(sqrt(broke ? sft : d), (T)0);
+      L[j * ld + j] = mk(sqrt(broke ? sft : d), (T)0);
     }
     __syncthreads();
-    const T inv = 1 / L[j * n + j].x;
+    const T inv = 1 / L[j * ld + j].x;
     for (int i = j + 1 + tid; i < n; i += blockDim.x)
-      L[i * n + j] = broke ? mk((T)0, (T)0) : cscale(L[i * n + j], inv);
+      L[i * ld + j] = broke ? mk((T)0, (T)0) : cscale(L[i * ld + j], inv);
     __syncthreads();
     const int m = n - j - 1;
     for (int idx = tid; idx < m * m; idx += blockDim.x) {        // trailing lower triangle
       int i = j + 1 + idx / m, k = j + 1 + idx % m;
       if (k > i) continue;
-      L[i * n + k] = csub(L[i * n + k], cmul(L[i * n + j], cconj(L[k * n + j])));
+      L[i * ld + k] = csub(L[i * ld + k], cmul(L[i * ld + j], cconj(L[k * ld + j])));
     }
     __syncthreads();
   }
-  // X = L^{-1}: column c by forward substitution (one thread per column)
-  for (int c = tid; c < n; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) X[i * n + c] = mk((T)0, (T)0);
-    for (int i = c; i < n; ++i) {
-      CT acc = mk(i == c ? (T)1 : (T)0, (T)0);
-      for (int k = c; k < i; ++k) acc = csub(acc, cmul(L[i * n + k], X[k * n + c]));
-      X[i * n + c] = cscale(acc, 1 / L[i * n + i].x);
+  // L <- L^{-1} in place, last column first
+  for (int j = n - 1; j >= 0; --j) {
+    const T d = 1 / L[j * ld + j].x;
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) xs[i] = L[i * ld + j];
+    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      CT acc = mk((T)0, (T)0);
+      for (int k = j + 1; k <= i; ++k) acc = cadd(acc, cmul(L[i * ld + k], xs[k]));
+      L[i * ld + j] = cscale(acc, -d);
     }
+    if (tid == 0) L[j * ld + j] = mk(d, (T)0);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {          // W = X^H
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {          // W = (L^{-1})^H
     int i = idx / n, j = idx % n;
-    W[idx] = from_cd<C>(to_cd(cconj(X[j * n + i])));
+    W[idx] = from_cd<C>(to_cd(j >= i ? cconj(L[j * ld + i]) : mk((T)0, (T)0)));
   }
 }
 
@@ -385,11 +395,12 @@ cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double s
   // reaches the shifts used at n ~ 100, which the pivot guard then absorbs.
   const bool c64 = !g_f64 && !w_f64;
   const bool f32 = c64 && fp32_factor;
+  if (n > CHOL_MAX_N) return cudaErrorInvalidValue;
   const size_t esz = f32 ? sizeof(cf) : sizeof(cd);
-  const size_t nn = (size_t)n * n * esz;
-  const int use_smem = 2 * nn <= SMEM_LIMIT ? 2 : (nn <= SMEM_LIMIT ? 1 : 0);
-  if (use_smem < 2 && !work) return cudaErrorInvalidValue;
-  const size_t sm = use_smem == 2 ? 2 * nn : (use_smem == 1 ? nn : 0);
+  const size_t need = (size_t)n * (n + 1) * esz;
+  const int use_smem = need <= SMEM_LIMIT ? 1 : 0;
+  if (!use_smem && !work) return cudaErrorInvalidValue;
+  const size_t sm = use_smem ? need : 0;
   cudaError_t ea = cudaSuccess;
   if (w_f64 && g_f64) ea = smem_optin((const void*)chol_w_kernel<cd, cd, double>, (int)SMEM_LIMIT);
   else if (g_f64) ea = smem_optin((const void*)chol_w_kernel<cf, cd, double>, (int)SMEM_LIMIT);
@@ -409,14 +420,14 @@ cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double s
   return cudaGetLastError();
 }
 
-bool chol_fits_smem(int n) { return (size_t)2 * n * n * sizeof(cd) <= SMEM_LIMIT; }
+bool chol_fits_smem(int n) { return (size_t)n * (n + 1) * sizeof(cd) <= SMEM_LIMIT; }
 
 cudaError_t eigh_batched(cd* A, long long sA, int lda, int n, int batch, double* lam, cd* V, long long sV, cd* work,
                          int* status, cudaStream_t st, int* sweeps_out) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   if (n > 512) return cudaErrorInvalidValue;  // round parameters held in 256-entry tables
   int np = n + (n & 1);
-  size_t bytes = (size_t)2 * np * np * sizeof(cd);
+  size_t bytes = (size_t)2 * np * (np + 1) * sizeof(cd);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
   cudaError_t ea = smem_optin((const void*)eigh_kernel<double>, (int)SMEM_LIMIT);
@@ -431,7 +442,7 @@ cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batc
   if (batch <= 0 || n <= 0) return cudaSuccess;
   if (n > 512) return cudaErrorInvalidValue;
   int np = n + (n & 1);
-  size_t bytes = (size_t)2 * np * np * sizeof(cf);
+  size_t bytes = (size_t)2 * np * (np + 1) * sizeof(cf);
   int use_smem = bytes <= SMEM_LIMIT;
   if (!use_smem && !work) return cudaErrorInvalidValue;
   cudaError_t ea = smem_optin((const void*)eigh_kernel<float>, (int)SMEM_LIMIT);
@@ -443,12 +454,12 @@ cudaError_t eigh_batched_f32(const cf* A, long long sA, int lda, int n, int batc
 
 bool eigh_fits_smem(int n) {
   size_t np = n + (n & 1);
-  return (size_t)2 * np * np * sizeof(cd) <= SMEM_LIMIT;
+  return (size_t)2 * np * (np + 1) * sizeof(cd) <= SMEM_LIMIT;
 }
 
 bool jacobi_fits_smem_f32(int n) {
   size_t np = n + (n & 1);
-  return (size_t)2 * np * np * sizeof(cf) <= SMEM_LIMIT;
+  return (size_t)2 * np * (np + 1) * sizeof(cf) <= SMEM_LIMIT;
 }
 
 cudaError_t svd_batched(cd* A, long long sA, int lda, int m, int n, int batch, double* sigma, cd* U, long long sU,

@@ -28,8 +28,8 @@ bool jacobi_fits_smem_f32(int n);
 // (g_f64) or complex64, W complex128 (w_f64) or complex64.  The factorisation runs
 // in FP64, except for complex64 G and W with fp32_factor (then FP32).  A pivot below
 // the shift (a Gram made indefinite by its rounding) is set to sqrt(shift) and its
-// column decoupled, so W stays bounded.  work: >= batch * 2 n^2 complex128 unless
-// chol_fits_smem(n).
+// column decoupled, so W stays bounded.  work: >= batch * n (n + 1) complex128 unless
+// chol_fits_smem(n) (callers may pass more).  n <= 512.
 cudaError_t chol_w_batched(const void* G, bool g_f64, int n, int batch, double shift, void* W, bool w_f64, void* work,
                            cudaStream_t st, bool fp32_factor = false);
 bool chol_fits_smem(int n);

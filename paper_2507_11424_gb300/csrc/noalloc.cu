@@ -26,10 +26,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 // by the context's unique id, so a second device, or the same device after
 // cudaDeviceReset (new primary context, module loaded again, possibly at another
 // address), looks the address up again instead of reusing a stale one.
-static std::map<unsigned long long, void*> g_scratch_addr;
+// Next to each address: the batch of the last call in that context, whose status
+// words (at the start of the array) tns_eigh_noalloc_status reads back.
+struct ScratchEntry {
+  void* addr;
+  int last_batch;
+};
+static std::map<unsigned long long, ScratchEntry> g_scratch_addr;
 static std::mutex g_scratch_mu;
 
-static tns_status scratch_address(void** out) {
+static tns_status scratch_entry(ScratchEntry** out) {
   unsigned long long ctx = 0;
   TNS_TRY_CUDA(current_context_id(&ctx));
   std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -38,9 +44,9 @@ static tns_status scratch_address(void** out) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    it = g_scratch_addr.emplace(ctx, p).first;
+    it = g_scratch_addr.emplace(ctx, ScratchEntry{p, 0}).first;
   }
-  *out = it->second;
+  *out = &it->second;   // std::map nodes do not move
   return TNS_OK;
 }
 
@@ -66,8 +72,9 @@ extern "C" tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A
               batch, n, n, status_bytes + work_bytes, NOALLOC_SCRATCH_BYTES);
     return TNS_ERR_ARG;
   }
-  void* base = nullptr;
-  TNS_TRY(scratch_address(&base));
+  ScratchEntry* se = nullptr;
+  TNS_TRY(scratch_entry(&se));
+  void* base = se->addr;
   int* status = static_cast<int*>(base);
   cd* work = work_bytes ? reinterpret_cast<cd*>(static_cast<unsigned char*>(base) + status_bytes) : nullptr;
   // Nothing in the scratch needs to start at zero: the kernel overwrites its
@@ -75,5 +82,34 @@ extern "C" tns_status tns_eigh_noalloc(int32_t batch, int32_t n, const double* A
   TNS_TRY_CUDA(eigh_batched(const_cast<cd*>(reinterpret_cast<const cd*>(A_dev)), (long long)n * n, n, n, batch, lam_dev,
                             reinterpret_cast<cd*>(V_dev), (long long)n * n, work, status,
                             static_cast<cudaStream_t>(cuda_stream)));
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    se->last_batch = batch;
+  }
+  return TNS_OK;
+}
+
+extern "C" tns_status tns_eigh_noalloc_status(int32_t batch, int32_t* status_dev, void* cuda_stream) {
+  if (batch < 0 || (batch > 0 && !status_dev)) {
+    set_error("invalid argument to tns_eigh_noalloc_status");
+    return TNS_ERR_ARG;
+  }
+  if (batch == 0) return TNS_OK;
+  ScratchEntry* se = nullptr;
+  TNS_TRY(scratch_entry(&se));
+  int last;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    last = se->last_batch;
+  }
+  if (batch > last) {
+    set_error("tns_eigh_noalloc_status: %d status words asked, the last tns_eigh_noalloc call on this device "
+              "wrote %d",
+              batch, last);
+    return TNS_ERR_ARG;
+  }
+  // stream-ordered device-to-device copy of the status words: no allocation, no host wait
+  TNS_TRY_CUDA(cudaMemcpyAsync(status_dev, se->addr, sizeof(int32_t) * (size_t)batch, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(cuda_stream)));
   return TNS_OK;
 }

@@ -162,7 +162,8 @@ template <typename C> __global__ void normalize_kernel(C* F, long long n) {
 // range-finder test matrices), the chunk's first sample index and the output buffers.
 struct SampleCall {
   uint64_t seed;
-  long long sample0;
+  long long sample0;     // the chunk's first row of the output buffers
+  long long first;       // stream index of output row 0 (Philox counter = first + row)
   uint8_t* bits;
   const uint8_t* forced;
   double* logq;
@@ -226,6 +227,7 @@ marginal_draw_kernel(const double* __restrict__ part, const C* __restrict__ G, i
   double* cond = call->cond;
   const uint64_t seed = call->seed;
   const long long sample0 = call->sample0;
+  const long long first = call->first;
   const int k = blockIdx.x;
   __shared__ int xs;
   __shared__ double invs;
@@ -244,7 +246,8 @@ marginal_draw_kernel(const double* __restrict__ part, const C* __restrict__ G, i
       if (forced) {
         x = forced[gs * n_sites + qubit] ? 1 : 0;
       } else {
-        Philox4 w = philox4x32_10((uint32_t)((uint64_t)gs & 0xffffffffu), (uint32_t)((uint64_t)gs >> 32),
+        const uint64_t ctr = (uint64_t)(first + gs);
+        Philox4 w = philox4x32_10((uint32_t)(ctr & 0xffffffffu), (uint32_t)(ctr >> 32),
                                   (uint32_t)qubit, 0u, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
         const double u = u53(w.v[0], w.v[1]);
         x = (u >= q0) ? 1 : 0;
@@ -980,7 +983,7 @@ static long long sampler_bytes_per_sample(tns_state* s, const Ctx& cx) {
   long long R = cx.R, chi = 1, rho = 1;
   for (int b = 0; b < s->H; ++b) chi = std::max(chi, row_chi(s, b));
   for (auto& E : s->env.E) rho = std::max(rho, env_rank(E));
-  long long kk = R + 8;
+  long long kk = R + cx.p;
   long long big = R * 2 * R * chi * rho;                 // marginal intermediates
   long long Tm = R * 2 * chi * R * chi;                  // zip matrix
   long long site = R * 2 * chi * R;                      // K' site
@@ -991,7 +994,7 @@ static long long sampler_bytes_per_sample(tns_state* s, const Ctx& cx) {
 }
 
 tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uint8_t* forced, uint8_t* bits,
-                  double* logq, double* cond) {
+                  double* logq, double* cond, long long first) {
   if (n == 0) return TNS_OK;
   Ctx cx;
   TNS_TRY(make_ctx(s, chi_b, seed, cx));
@@ -1164,7 +1167,7 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
   };
   for (long long s0 = 0; s0 < n; s0 += chunk) {
     const long long S = std::min(chunk, n - s0);
-    SampleCall hc{seed, s0, bits, forced, logq, cond};
+    SampleCall hc{seed, s0, first, bits, forced, logq, cond};
     static_assert(sizeof(SampleCall) <= sizeof(s->host_call), "call block staging");
     memcpy(s->host_call, &hc, sizeof hc);
     TNS_TRY_CUDA(cudaMemcpyAsync(dcall, s->host_call, sizeof hc, cudaMemcpyHostToDevice, cx.st));
@@ -1205,7 +1208,8 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         return rs;
       }
       TNS_TRY_CUDA(ec);
-      // kernels recorded during capture were counted but not launched; the graph's
+      // kernels recorded during capture were counted but not launched (the contraction
+      // layer's count reaches s->launches when the API call returns); the graph's
       // launches are counted on every replay instead
       tns_state::GraphEntry en;
       const long long cdelta = contract_launches() - c0;

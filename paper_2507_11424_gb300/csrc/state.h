@@ -140,8 +140,19 @@ tns_status apply_gate_layer(tns_state* s, int n_gates, const int32_t* sites, con
                             double cutoff, double* eps_out);
 tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* resid);
 // sampler.cu
+// Attributes the contraction launches made by this thread during an API call to
+// the call's state (the contraction layer counts per thread, not per state).
+struct LaunchScope {
+  tns_state* s;
+  long long c0;
+  explicit LaunchScope(tns_state* st) : s(st), c0(contract_launches()) {}
+  ~LaunchScope() {
+    if (s) s->launches += contract_launches() - c0;
+  }
+};
+
 tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uint8_t* forced, uint8_t* bits,
-                  double* logq, double* cond);
+                  double* logq, double* cond, long long first = 0);
 tns_status amplitude(tns_state* s, int chi_b, long long n, const uint8_t* bits, double* log_abs, double* phase);
 tns_status log_norm(tns_state* s, int chi_b, double* out);
 tns_status direct_marginals(tns_state* s, int chi_b, double* one, double* two);

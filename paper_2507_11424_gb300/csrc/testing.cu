@@ -225,3 +225,32 @@ extern "C" tns_status tns_test_plan(const char* labels_a, const int64_t* dims_a,
   for (int i = 0; i < 11; ++i) out[i] = o[i];
   return TNS_OK;
 }
+
+extern "C" tns_status tns_test_env_site(tns_state* s, int32_t b, int32_t k, int64_t* dims_out, int32_t* reversed_out,
+                                        double* out_host) {
+  if (!s || !dims_out) { set_error("invalid argument"); return TNS_ERR_ARG; }
+  const EnvCache& ec = s->env;
+  if (!ec.valid) { set_error("no environment cached"); return TNS_ERR_STATE; }
+  if (b < 0 || b >= (int)ec.E.size() || k < 0 || k >= (int)ec.E[b].site.size()) {
+    set_error("env site index out of range");
+    return TNS_ERR_ARG;
+  }
+  const StoredMPS& m = ec.E[b];
+  if (m.phys[k].size() != 2) { set_error("env site with %zu physical legs", m.phys[k].size()); return TNS_ERR_STATE; }
+  dims_out[0] = m.bond[k];
+  dims_out[1] = m.phys[k][0];
+  dims_out[2] = m.phys[k][1];
+  dims_out[3] = m.bond[k + 1];
+  if (reversed_out) *reversed_out = m.reversed ? 1 : 0;
+  if (!out_host) return TNS_OK;
+  const long long n = dims_out[0] * dims_out[1] * dims_out[2] * dims_out[3];
+  TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
+  if (ec.prec == 0) {
+    TNS_TRY_CUDA(cudaMemcpy(out_host, m.site[k], sizeof(cd) * n, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> tmp(2 * n);
+    TNS_TRY_CUDA(cudaMemcpy(tmp.data(), m.site[k], sizeof(cf) * n, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < 2 * n; ++i) out_host[i] = tmp[i];
+  }
+  return TNS_OK;
+}

@@ -59,7 +59,7 @@ def test_device_eigh(env, n, batch):
         assert np.abs(A[b] @ V[b] - V[b] * lam[b]).max() < 1e-11 * scale
 
 
-@pytest.mark.parametrize("n,batch", [(1, 3), (7, 5), (72, 3), (81, 2), (136, 2), (200, 2)])
+@pytest.mark.parametrize("n,batch", [(1, 3), (7, 5), (72, 3), (81, 2), (112, 2), (113, 2), (136, 2), (200, 2)])
 def test_device_eigh_fp32(env, n, batch):
     """FP32 Jacobi (mixed-precision truncation) on complex64 input: backward error of
     a Jacobi method is a modest multiple of n eps ||A|| (eps = 2^-24)."""
@@ -111,7 +111,7 @@ def test_device_svd(env, m, n, batch):
         assert np.abs(V[b].conj().T @ V[b] - np.eye(n)).max() < 1e-12
 
 
-@pytest.mark.parametrize("n,batch,rank", [(72, 3, 72), (72, 2, 50), (264, 2, 256)])
+@pytest.mark.parametrize("n,batch,rank", [(72, 3, 72), (72, 2, 50), (112, 2, 112), (113, 2, 100), (264, 2, 256)])
 def test_device_cholesky_orthonormaliser(env, n, batch, rank):
     """Y W has orthonormal columns on range(Y) when W comes from the shifted Cholesky of Y^H Y."""
     torch, lib = env

@@ -299,3 +299,23 @@ def test_graph_replay_equals_eager(pkg, tmp_path, prec):
         assert torch.equal(ra[1], rb[1]) and torch.equal(ra[1], a[2])
     # a replayed graph counts the kernels it launches
     assert st_g.launch_count() == st_e.launch_count()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sample_range_is_a_slice_of_the_stream(pkg, tmp_path, prec):
+    """tns_sample_range(first, n) returns rows first .. first + n - 1 of the stream that
+    tns_sample draws with the same seed, bit for bit (the sharding rule of the
+    multi-device sampler), whatever the chunk it is drawn in."""
+    import torch
+    lat = w.square(4, 4)
+    bits = w.domain_wall_bits(lat)
+    t = oracle_state(lat, bits, w.heisenberg_circuit(lat, 4, 0.2), 4)
+    st = to_gpu(pkg, t, tmp_path, prec, "r.tnsf")
+    full = st.sample(16, 20, 99, cond=True)
+    for first, n in ((0, 7), (7, 6), (13, 7), (19, 1)):
+        part = st.sample(16, n, 99, cond=True, first=first)
+        for x, y in zip(part, full):
+            assert torch.equal(x, y[first:first + n])
+    with pytest.raises(pkg.TNSError):
+        st.sample(16, 2, 99, first=-1)
+    st.close()

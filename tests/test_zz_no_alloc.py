@@ -50,6 +50,12 @@ def test_noalloc_eigh_matches_allocating_entry_point(env, n, batch):
         lc = lam.cpu().numpy()
         for b in range(batch):
             assert np.abs(A[b] @ Vc[b] - Vc[b] * lc[b]).max() < 1e-11 * scale
+        # every matrix converged, and the status query reads that back
+        st = torch.full((batch,), -1, dtype=torch.int32, device="cuda")
+        assert lib.tns_eigh_noalloc_status(batch, _ptr(st), stream) == 0
+        torch.cuda.synchronize()
+        assert st.tolist() == [0] * batch
+    assert lib.tns_eigh_noalloc_status(batch + 1, _ptr(st), stream) == 1
 
 
 def test_noalloc_rejects_batches_beyond_the_static_scratch(env):
