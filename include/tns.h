@@ -101,9 +101,30 @@ tns_status tns_apply_gate_layer(tns_state* s, int32_t n_gates, const int32_t* si
  * with all messages into v except the one from v', Hermitised and normalised to
  * unit Frobenius norm, until max |m_new - m_old|_F < tol or max_iter sweeps.
  *   iters_out, residual_out  host pointers or NULL.
+ * Precision: in TNS_PREC_FP64 every contraction is FP64.  In TNS_PREC_MIXED the
+ * message contractions run on complex64 copies of the site tensors and messages
+ * (TF32x3 tensor cores, FP32 accumulation) while the Hermitisation, normalisation,
+ * residual and the stored messages stay FP64.  The residual of the mixed path cannot
+ * fall much below the FP32 rounding of those contractions: a tol below 1e-6 is
+ * raised to 1e-6, and a residual under 1e-3 that stops falling (less than a 10% gain
+ * over its best for 5 iterations) counts as converged at that floor.
+ * The host checks the residual of iteration i while iteration i + 1 runs, so
+ * iters_out may exceed the first iteration below tol by one.
  * Returns TNS_ERR_NOT_CONVERGED (state still valid) when max_iter is reached.
  */
 tns_status tns_bp_gauge(tns_state* s, int32_t max_iter, double tol, int32_t* iters_out, double* residual_out);
+
+/*
+ * tns_bp_stats -- measurements of the last tns_bp_gauge call on this state:
+ *   device_ms  elapsed device time of all its iterations (CUDA events on the state's
+ *              stream, from the first launch to the last residual copy)
+ *   bytes      algorithmic bytes: per iteration and directed edge, the site tensor
+ *              (read once for ket and bra), the incoming messages and the new message,
+ *              in the path's element size (16 B FP64, 8 B mixed)
+ *   flops      algorithmic real flops of the message contractions (8 per complex MAC)
+ * Any pointer may be NULL.  All zero before the first call.
+ */
+tns_status tns_bp_stats(const tns_state* s, double* device_ms, double* bytes, double* flops);
 
 /*
  * tns_sample -- draw n_samples bitstrings with the boundary-MPS sampler (Appendix,

@@ -107,6 +107,12 @@ class TNSState:
               "tns_bp_gauge", allow)
         return it.value, res.value
 
+    def bp_stats(self) -> dict:
+        """Device time, algorithmic bytes and flops of the last bp_gauge call."""
+        ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+        check(self.lib.tns_bp_stats(self._h, C.byref(ms), C.byref(by), C.byref(fl)), "tns_bp_stats")
+        return {"ms": ms.value, "bytes": by.value, "flops": fl.value}
+
     def log_fidelity(self) -> float:
         v = C.c_double()
         check(self.lib.tns_log_fidelity(self._h, C.byref(v)), "tns_log_fidelity")

@@ -32,6 +32,7 @@ SIGNATURES = {
                                     C.c_void_p]),
     "tns_amplitude": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tns_log_fidelity": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "tns_bp_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tns_log_norm": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
     "tns_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "tns_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),

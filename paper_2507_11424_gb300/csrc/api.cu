@@ -143,6 +143,8 @@ static void free_state(tns_state* s) {
   for (auto& e : s->gev)
     if (e) cudaEventDestroy(e);
   if (s->gstream) cudaStreamDestroy(s->gstream);
+  if (s->bp_host) cudaFreeHost(s->bp_host);
+  s->bp_host = nullptr;
   for (auto* ec : {&s->env, &s->env_top})
     for (auto& E : ec->E)
       for (auto p : E.site)
@@ -330,6 +332,14 @@ extern "C" tns_status tns_certify(tns_state* s, int32_t chi_b, int64_t n, const 
     return TNS_ERR_ARG;
   }
   return certify(s, chi_b, n, bits_dev, logq_dev, logp_dev, stats_host);
+}
+
+extern "C" tns_status tns_bp_stats(const tns_state* s, double* ms, double* bytes, double* flops) {
+  if (!s) { set_error("invalid argument to tns_bp_stats"); return TNS_ERR_ARG; }
+  if (ms) *ms = s->bp_last_ms;
+  if (bytes) *bytes = s->bp_last_bytes;
+  if (flops) *flops = s->bp_last_flops;
+  return TNS_OK;
 }
 
 extern "C" tns_status tns_log_fidelity(const tns_state* s, double* log_f) {

@@ -50,9 +50,12 @@ cudaError_t current_context_id(unsigned long long* id) {
   CUcontext ctx = nullptr;
   if (f.get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
   if (!ctx) {
-    // no context bound to this thread yet: cudaFree(0) makes the runtime bind the
-    // device's primary context (only on this first call, never during a capture)
-    cudaError_t e = cudaFree(nullptr);
+    // no context bound to this thread yet: cudaSetDevice on the current device makes
+    // the runtime create and bind its primary context (CUDA 12 and later), without
+    // touching any allocator (only on this first call, never during a capture)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e != cudaSuccess) return e;
     if (f.get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
   }

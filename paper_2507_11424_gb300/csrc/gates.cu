@@ -1,5 +1,7 @@
 // BP-gauged simple update (Methods, Eqs. 1-2; Appendix Fig. 8d) and belief
-// propagation (Appendix Fig. 8c) on the device, FP64 throughout.
+// propagation (Appendix Fig. 8c) on the device.  Gates are FP64 throughout; BP is
+// FP64 in the FP64 path and complex64 contractions with FP64 normalisation in the
+// mixed path.
 #include <cctype>
 #include <cmath>
 #include <algorithm>
@@ -12,6 +14,12 @@
 namespace tns {
 
 static const char LEGCH[5] = {'s', 'u', 'l', 'd', 'r'};
+
+// Mixed-path BP (complex64 contractions, FP64 normalisation): smallest tolerance
+// honoured, and the stall rule that detects the FP32 rounding floor.
+static constexpr double BP_MIXED_FLOOR = 1e-6;
+static constexpr double BP_MIXED_STALL_BELOW = 1e-3;
+static constexpr int BP_MIXED_STALL_ITERS = 5;
 
 static std::vector<long long> dims5(const int d[5]) { return {d[0], d[1], d[2], d[3], d[4]}; }
 
@@ -73,10 +81,19 @@ struct MsgDesc {
   cd* cur;
   cd* nw;
   int D;
+  const cf* nw32;    // mixed path: the new message in complex64 (read instead of nw)
 };
 
-// Hermitise and normalise every new message, write it over the current one and
-// record |m_new - m_old|_F per message.
+__device__ __forceinline__ cd bp_new_entry(const MsgDesc& d, int idx) {
+  if (d.nw32) {
+    const cf v = d.nw32[idx];
+    return mk((double)v.x, (double)v.y);
+  }
+  return d.nw[idx];
+}
+
+// Hermitise and normalise every new message in FP64, write it over the current
+// one and record |m_new - m_old|_F per message.  One block per message.
 __global__ void bp_finish_kernel(const MsgDesc* md, double* resid) {
   MsgDesc d = md[blockIdx.x];
   __shared__ double red[256];
@@ -84,7 +101,7 @@ __global__ void bp_finish_kernel(const MsgDesc* md, double* resid) {
   double s2 = 0.0;
   for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
     int i = idx / D, j = idx % D;
-    cd a = d.nw[i * D + j], b = cconj(d.nw[j * D + i]);
+    cd a = bp_new_entry(d, i * D + j), b = cconj(bp_new_entry(d, j * D + i));
     s2 += cabs2(cscale(cadd(a, b), 0.5));
   }
   red[threadIdx.x] = s2;
@@ -99,7 +116,7 @@ __global__ void bp_finish_kernel(const MsgDesc* md, double* resid) {
   double df = 0.0;
   for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
     int i = idx / D, j = idx % D;
-    cd a = d.nw[i * D + j], b = cconj(d.nw[j * D + i]);
+    cd a = bp_new_entry(d, i * D + j), b = cconj(bp_new_entry(d, j * D + i));
     cd h = cscale(cadd(a, b), 0.5 * inv);
     cd o = d.cur[idx];
     df += cabs2(csub(h, o));
@@ -115,6 +132,16 @@ __global__ void bp_finish_kernel(const MsgDesc* md, double* resid) {
 }
 
 static inline int blocks(long long n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// complex128 -> complex64 copy (the mixed path's BP operands)
+__global__ void bp_to_c64_kernel(const cd* __restrict__ in, cf* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cd v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+static inline int grid_stride_blocks(long long n) { return (int)std::min<long long>(4 * 152, std::max(1LL, (n + 255) / 256)); }
 
 // t'[.. J ..] = sum_j t[.. j ..] M[j, J] on axis `leg` of a [s][u][l][d][r] tensor.
 static cudaError_t apply_leg(const cd* src, const int d[5], int leg, const cd* M, cd* dst, cudaStream_t st) {
@@ -446,7 +473,18 @@ tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* 
   }
   *iters = 0;
   *resid = 0.0;
+  s->bp_last_ms = s->bp_last_bytes = s->bp_last_flops = 0.0;
   if (md.empty()) return TNS_OK;
+  // Precision: FP64 path, every contraction in FP64.  Mixed path, the message
+  // contractions run on complex64 copies of the cells and messages (TF32x3 tensor
+  // cores where the planner finds them worth it, FP32 CUDA cores otherwise, FP32
+  // accumulation) and the Hermitisation, normalisation and residual stay FP64; the
+  // residual then cannot fall much below the FP32 rounding of the contractions, so
+  // the tolerance is raised to BP_MIXED_FLOOR.
+  const bool mixed = s->prec == TNS_PREC_MIXED;
+  const Prec bp_prec = mixed ? (s->tensor_cores ? Prec::TF32X3 : Prec::F32) : Prec::F64;
+  const double tol_eff = mixed ? std::max(tol, BP_MIXED_FLOOR) : tol;
+  const size_t esz = mixed ? sizeof(cf) : sizeof(cd);
   // upload the offset tables once
   std::vector<long long> table;
   for (auto& g : groups) {
@@ -458,6 +496,7 @@ tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* 
   TNS_TRY_CUDA(s->ws.get("bp_tab", sizeof(long long) * table.size(), (void**)&dtab));
   TNS_TRY_CUDA(cudaMemcpyAsync(dtab, table.data(), sizeof(long long) * table.size(), cudaMemcpyHostToDevice, st));
   long long pos = 0, xmax = 1;
+  double bytes_it = 0.0;
   for (auto& g : groups) {
     const long long G = (long long)g.cell_off.size();
     g.d_cell = dtab + pos; pos += G;
@@ -465,41 +504,98 @@ tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* 
     for (int leg = 1; leg <= 4; ++leg) { g.d_moff[leg] = dtab + pos; pos += G; }
     long long sz = (long long)g.dims[0] * g.dims[1] * g.dims[2] * g.dims[3] * g.dims[4];
     xmax = std::max(xmax, G * sz);
+    // algorithmic bytes: every member reads its site tensor (ket and bra side of the
+    // same array, counted once), its incoming messages, and writes one message
+    long long mb = 0;
+    for (int leg = 1; leg <= 4; ++leg)
+      if (leg != g.j && (g.edges >> leg & 1)) mb += (long long)g.dims[leg] * g.dims[leg];
+    mb += (long long)g.dims[g.j] * g.dims[g.j];
+    bytes_it += (double)G * (double)(sz + mb) * (double)esz;
   }
-  cd *X0, *X1;
-  TNS_TRY_CUDA(s->ws.get("bp_X0", sizeof(cd) * xmax, (void**)&X0));
-  TNS_TRY_CUDA(s->ws.get("bp_X1", sizeof(cd) * xmax, (void**)&X1));
+  void *X0, *X1;
+  TNS_TRY_CUDA(s->ws.get("bp_X0", esz * xmax, &X0));
+  TNS_TRY_CUDA(s->ws.get("bp_X1", esz * xmax, &X1));
+  void* cells = s->cell_arena;
+  void* msgs = s->msg_arena;
+  void* msgs_new = s->msg_new_arena;
+  const long long msg_elems = mslot * (long long)s->cell.size() * 5;
+  cf* m32 = nullptr;
+  if (mixed) {
+    long long arena = 0;
+    for (auto& c : s->cell) arena = std::max(arena, c.off + c.cap);
+    cf *c32 = nullptr, *mn32 = nullptr;
+    TNS_TRY_CUDA(s->ws.get("bp_c32", sizeof(cf) * arena, (void**)&c32));
+    TNS_TRY_CUDA(s->ws.get("bp_m32", sizeof(cf) * msg_elems, (void**)&m32));
+    TNS_TRY_CUDA(s->ws.get("bp_mn32", sizeof(cf) * msg_elems, (void**)&mn32));
+    bp_to_c64_kernel<<<grid_stride_blocks(arena), 256, 0, st>>>(s->cell_arena, c32, arena);
+    s->launches++;
+    cells = c32;
+    msgs = m32;
+    msgs_new = mn32;
+    for (auto& d : md) d.nw32 = mn32 + (d.nw - s->msg_new_arena);
+  }
   MsgDesc* dmd = nullptr;
   double* dres = nullptr;
-  TNS_TRY_CUDA(s->ws.get("bp_desc", sizeof(MsgDesc) * md.size(), (void**)&dmd));
-  TNS_TRY_CUDA(s->ws.get("bp_res", sizeof(double) * md.size(), (void**)&dres));
-  TNS_TRY_CUDA(cudaMemcpyAsync(dmd, md.data(), sizeof(MsgDesc) * md.size(), cudaMemcpyHostToDevice, st));
-  std::vector<double> hres(md.size());
+  const size_t nmsg = md.size();
+  TNS_TRY_CUDA(s->ws.get("bp_desc", sizeof(MsgDesc) * nmsg, (void**)&dmd));
+  TNS_TRY_CUDA(s->ws.get("bp_res", sizeof(double) * nmsg, (void**)&dres));
+  TNS_TRY_CUDA(cudaMemcpyAsync(dmd, md.data(), sizeof(MsgDesc) * nmsg, cudaMemcpyHostToDevice, st));
+  if (s->bp_host_n < 2 * nmsg) {
+    if (s->bp_host) cudaFreeHost(s->bp_host);
+    s->bp_host = nullptr;
+    s->bp_host_n = 0;
+    TNS_TRY_CUDA(cudaMallocHost((void**)&s->bp_host, sizeof(double) * 2 * nmsg));
+    s->bp_host_n = 2 * nmsg;
+  }
+  double* hres[2] = {s->bp_host, s->bp_host + nmsg};
+  // events: two per iteration slot (residual copy landed), plus the timing pair
+  cudaEvent_t ev[2] = {nullptr, nullptr}, t0 = nullptr, t1 = nullptr;
+  struct EvGuard {
+    cudaEvent_t* e[4];
+    ~EvGuard() {
+      for (auto p : e)
+        if (*p) cudaEventDestroy(*p);
+    }
+  } guard{{&ev[0], &ev[1], &t0, &t1}};
+  for (auto& e : ev) TNS_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  TNS_TRY_CUDA(cudaEventCreate(&t0));
+  TNS_TRY_CUDA(cudaEventCreate(&t1));
+  TNS_TRY_CUDA(cudaEventRecord(t0, st));
+  double flops_it = 0.0;
   const std::string lab = "suldr";
-  for (int it = 1; it <= max_iter; ++it) {
+  // one BP iteration: contractions for every directed edge, FP64 finish, residuals
+  // copied to hres[slot] (pinned) and ev[slot] recorded; nothing waits on the host
+  auto enqueue = [&](int slot) -> tns_status {
+    if (mixed) {
+      bp_to_c64_kernel<<<grid_stride_blocks(msg_elems), 256, 0, st>>>(s->msg_arena, m32, msg_elems);
+      s->launches++;
+    }
+    double fl_total = 0.0;
     for (auto& g : groups) {
       const long long G = (long long)g.cell_off.size();
       std::vector<long long> d5 = dims5(g.dims);
       std::vector<long long> gd = {G};
       gd.insert(gd.end(), d5.begin(), d5.end());
-      const long long sz = d5[0] * d5[1] * d5[2] * d5[3] * d5[4];
       // current operand: the cells themselves (gathered) or a workspace buffer
-      TView cur = view(s->cell_arena, "G" + lab, gd);
+      TView cur = view(cells, "G" + lab, gd);
       cur.stride[0] = 0;
       cur.boff = g.d_cell;
       cur.boff_label = 'G';
-      cd* bufs[2] = {X0, X1};
+      void* bufs[2] = {X0, X1};
       int nb = 0;
+      double fl = 0.0;
       for (int leg = 1; leg <= 4; ++leg) {
         if (leg == g.j || !(g.edges >> leg & 1)) continue;
         std::string out = "G" + lab;
         out[leg + 1] = (char)toupper(lab[leg]);
-        TView M = view(s->msg_arena, std::string("G") + lab[leg] + out[leg + 1], {G, d5[leg], d5[leg]});
+        TView M = view(msgs, std::string("G") + lab[leg] + out[leg + 1], {G, d5[leg], d5[leg]});
         M.stride[0] = 0;
         M.boff = g.d_moff[leg];
         M.boff_label = 'G';
-        cd* dst = bufs[nb & 1];
-        TNS_TRY_CUDA(contract(cur, M, view(dst, out, gd), Prec::F64, st));
+        void* dst = bufs[nb & 1];
+        TNS_TRY_CUDA(contract(cur, M, view(dst, out, gd), bp_prec, st, make_double2(1.0, 0.0),
+                              make_double2(0.0, 0.0), &fl));
+        fl_total += fl;
         cur = view(dst, "G" + lab, gd);   // labels restart for the next leg
         ++nb;
       }
@@ -507,33 +603,82 @@ tns_status bp_gauge(tns_state* s, int max_iter, double tol, int* iters, double* 
       la[g.j + 1] = 'a';
       lb[g.j + 1] = 'b';
       cur.labels = la;
-      TView bra = view(s->cell_arena, lb, gd, true);
+      TView bra = view(cells, lb, gd, true);
       bra.stride[0] = 0;
       bra.boff = g.d_cell;
       bra.boff_label = 'G';
       const long long D = d5[g.j];
-      TView out = view(s->msg_new_arena, "Gab", {G, D, D});
+      TView out = view(msgs_new, "Gab", {G, D, D});
       out.stride[0] = 0;
       out.boff = g.d_dst;
       out.boff_label = 'G';
-      TNS_TRY_CUDA(contract(cur, bra, out, Prec::F64, st));
-      (void)sz;
+      TNS_TRY_CUDA(contract(cur, bra, out, bp_prec, st, make_double2(1.0, 0.0), make_double2(0.0, 0.0), &fl));
+      fl_total += fl;
     }
-    bp_finish_kernel<<<(unsigned)md.size(), 256, 0, st>>>(dmd, dres);
+    flops_it = fl_total;
+    bp_finish_kernel<<<(unsigned)nmsg, 256, 0, st>>>(dmd, dres);
     s->launches++;
-    TNS_TRY_CUDA(cudaMemcpyAsync(hres.data(), dres, sizeof(double) * md.size(), cudaMemcpyDeviceToHost, st));
-    TNS_TRY_CUDA(cudaStreamSynchronize(st));
+    TNS_TRY_CUDA(cudaMemcpyAsync(hres[slot], dres, sizeof(double) * nmsg, cudaMemcpyDeviceToHost, st));
+    TNS_TRY_CUDA(cudaEventRecord(ev[slot], st));
+    return TNS_OK;
+  };
+  // residual of the iteration whose copy went to hres[slot] (waits for that copy only)
+  auto residual = [&](int slot, double* r) -> tns_status {
+    TNS_TRY_CUDA(cudaEventSynchronize(ev[slot]));
     double mx = 0.0;
-    for (double x : hres) {
-      if (!std::isfinite(x)) { set_error("non-finite BP message"); *iters = it; *resid = x; return TNS_ERR_NUMERIC; }
+    for (size_t i = 0; i < nmsg; ++i) {
+      const double x = hres[slot][i];
+      if (!std::isfinite(x)) { *r = x; set_error("non-finite BP message"); return TNS_ERR_NUMERIC; }
       mx = std::max(mx, x);
     }
+    *r = mx;
+    return TNS_OK;
+  };
+  auto finish = [&](int it, double r) {
     *iters = it;
-    *resid = mx;
-    if (mx < tol) return TNS_OK;
+    *resid = r;
+    float ms = 0.f;
+    if (cudaEventRecord(t1, st) == cudaSuccess && cudaEventSynchronize(t1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess)
+      s->bp_last_ms = ms;
+    s->bp_last_bytes = bytes_it * it;
+    s->bp_last_flops = flops_it * it;
+  };
+  // Iteration it is checked while iteration it + 1 runs, so the host never idles the
+  // GPU; convergence is declared on the last enqueued iteration.  Mixed path: once the
+  // residual is below BP_MIXED_STALL_BELOW and has stopped falling (no 10% gain over
+  // the best for BP_MIXED_STALL_ITERS checks) it sits at the FP32 rounding floor, which
+  // also counts as converged.
+  double best = 1e300;
+  int stall = 0;
+  for (int it = 1;; ++it) {
+    TNS_TRY(enqueue(it & 1));
+    double r = 0.0;
+    if (it > 1) {
+      TNS_TRY(residual((it - 1) & 1, &r));
+      bool floor_hit = false;
+      if (mixed) {
+        stall = (r < BP_MIXED_STALL_BELOW && r > 0.9 * best) ? stall + 1 : 0;
+        best = std::min(best, r);
+        floor_hit = stall >= BP_MIXED_STALL_ITERS;
+      }
+      if (r < tol_eff || floor_hit) {
+        double r2 = 0.0;
+        TNS_TRY(residual(it & 1, &r2));
+        if (r2 < tol_eff || floor_hit) {
+          finish(it, r2);
+          return TNS_OK;
+        }
+      }
+    }
+    if (it >= max_iter) {
+      TNS_TRY(residual(it & 1, &r));
+      finish(it, r);
+      if (r < tol_eff) return TNS_OK;
+      set_error("BP not converged after %d iterations (residual %.3e)", max_iter, r);
+      return TNS_ERR_NOT_CONVERGED;
+    }
   }
-  set_error("BP not converged after %d iterations (residual %.3e)", max_iter, *resid);
-  return TNS_ERR_NOT_CONVERGED;
 }
 
 }  // namespace tns

@@ -585,7 +585,8 @@ static tns_status wsget(tns_state* s, const char* nm, size_t bytes, void** p) {
 // Q = orthonormal basis of range(Y) for each batch entry (Y, Q: S x M x kk).
 // FP64 path: W = L^{-H} with L L^H = Y^H Y + 1e-14 max_i G_ii (the shift only
 // regularises rank-deficient Y), Q = Y W.  Mixed path: shifted CholeskyQR3 in
-// FP32 (Gram and products in FP32, the kk x kk Cholesky in FP64), every pass with
+// FP32 (Gram and products in FP32, the first pass's kk x kk Cholesky in FP64, the
+// later two in FP32), every pass with
 // shift 1e-5: the first gives a well-conditioned basis of the same range, the two
 // more restore orthonormality to ~1e-5 (directions with Gram eigenvalue below the
 // shift are damped, not lost).
@@ -612,9 +613,12 @@ static tns_status orth(Ctx& cx, void* Y, long long S, long long M, int kk, void*
   if (span_only) return pass(Y, Qout, ORTH_SHIFT_CQR_FIRST, true);
   void* tmp;
   TNS_TRY(wsget(s, "z_Q2", cx.esz * S * M * kk, &tmp));
+  // the first pass sees the Gram of Y (condition up to ~1/shift) and factorises in
+  // FP64; the two more see the Gram of an already well-conditioned basis (close to
+  // the identity), whose FP32 Cholesky is as accurate as the FP32 Gram it factorises
   TNS_TRY(pass(Y, Qout, ORTH_SHIFT_CQR_FIRST, false));
-  TNS_TRY(pass(Qout, tmp, ORTH_SHIFT_CQR_NEXT, false));
-  return pass(tmp, Qout, ORTH_SHIFT_CQR_NEXT, false);
+  TNS_TRY(pass(Qout, tmp, ORTH_SHIFT_CQR_NEXT, true));
+  return pass(tmp, Qout, ORTH_SHIFT_CQR_NEXT, true);
 }
 
 // Rank-R factorisation T = K C of each batch entry (T: S x M x N): randomized

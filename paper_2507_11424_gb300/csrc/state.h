@@ -112,6 +112,14 @@ struct tns_state {
   cudaStream_t gstream = nullptr;       // private stream that graphs are captured and replayed on
   cudaEvent_t gev[2] = {nullptr, nullptr};
   long long work_version = -1;
+  // pinned host buffer for BP's per-message residuals (two iterations in flight)
+  double* bp_host = nullptr;
+  size_t bp_host_n = 0;
+  // BP timing of the last tns_bp_gauge call: iterations and device milliseconds of the
+  // message contractions + normalisation (events on the state's stream)
+  double bp_last_ms = 0.0;
+  double bp_last_bytes = 0.0;   // algorithmic bytes of the last call (site tensors + messages)
+  double bp_last_flops = 0.0;
 
   int cidx(int r, int c) const { return r * W + c; }
   void nbr(int ci, int leg, int& r2, int& c2) const {

@@ -117,6 +117,32 @@ def test_bp_reports_iterations_and_converges(pkg):
     st.bp_gauge(500, 1e-12)
 
 
+def test_mixed_bp_reaches_the_fp64_fixed_point(pkg):
+    """Mixed-path BP (complex64 message contractions on the tensor cores, FP64
+    Hermitisation and normalisation) against FP64 BP on the same circuit: 6x6 square
+    lattice, 3 Heisenberg layers at chi = 16 (the third truncates), so the message contractions of the
+    interior cells are large enough for the tensor cores.  The BP fixed point sets the
+    gauge of every truncated gate, so per-gate truncation errors (Eq. 1) and log f
+    (Eq. 2) agree to the FP32 rounding floor of the mixed messages; the device time,
+    bytes and flops of the last call are reported."""
+    lat = w.square(6, 6)
+    bits = w.domain_wall_bits(lat)
+    groups = w.heisenberg_circuit(lat, 3, 0.2)
+    st64, eps64 = gpu_state(pkg, lat, bits, groups, 16, prec="fp64")
+    st32, eps32 = gpu_state(pkg, lat, bits, groups, 16, prec="mixed")
+    assert eps64.max() > 1e-4
+    assert np.abs(eps32 - eps64).max() < 2e-5, np.abs(eps32 - eps64).max()
+    assert abs(st32.log_fidelity() - st64.log_fidelity()) < 1e-4, (st32.log_fidelity(), st64.log_fidelity())
+    # a fresh gate group, then a full mixed BP run from the stale messages
+    st32.apply_gate_layer(w.heisenberg_circuit(lat, 1, 0.2)[0], chi=16)
+    it, res = st32.bp_gauge(200, 1e-10)
+    assert it >= 2 and res < 1e-3
+    stats = st32.bp_stats()
+    assert stats["ms"] > 0 and stats["bytes"] > 0 and stats["flops"] > 0
+    st32.close()
+    st64.close()
+
+
 def test_invalid_gate_layers_rejected(pkg):
     from paper_2507_11424_gb300 import TNSError
     lat = w.square(3, 3)

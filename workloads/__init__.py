@@ -7,7 +7,7 @@ not implement any step of the tensor-network simulation or sampling method.
 from .lattices import Lattice, square, heavy_hex, ladder, edge_index  # noqa: F401
 from .circuits import (  # noqa: F401
     heisenberg_gate, givens_gate, phase_gate, cphase_gate, domain_wall_bits,
-    heisenberg_circuit, lucj_like_circuit, random_su4_circuit, flatten_group,
+    heisenberg_circuit, disordered_heisenberg_circuit, lucj_like_circuit, random_su4_circuit, flatten_group,
 )
 
 from .made_init import made_init, epoch_orders  # noqa: F401

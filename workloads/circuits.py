@@ -66,6 +66,22 @@ def heisenberg_circuit(lat: Lattice, layers: int, dt: float, J: float = 1.0) -> 
     return groups
 
 
+def disordered_heisenberg_circuit(lat: Lattice, layers: int, dt: float, seed: int, spread: float = 0.2) -> list:
+    """The Trotter circuit of heisenberg_circuit with one coupling J_e per bond, drawn
+    once from U[1 - spread, 1 + spread] (seeded, PCG64).  Random couplings remove the
+    lattice symmetries of the uniform quench, whose truncations meet exactly degenerate
+    singular values (so the truncated state depends on rounding); here every cut is
+    generic and the state is reproducible across platforms."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    J = rng.uniform(1.0 - spread, 1.0 + spread, size=len(lat.edges))
+    gates = [heisenberg_gate(dt, float(j)) for j in J]
+    groups = []
+    for _ in range(layers):
+        for col in lat.colors:
+            groups.append([(int(lat.edges[e][0]), int(lat.edges[e][1]), gates[e]) for e in col])
+    return groups
+
+
 def lucj_like_circuit(lat: Lattice, reps: int = 3, seed: int = 11424) -> tuple[list, np.ndarray]:
     """LUCJ-shaped ladder circuit (synthetic stand-in for the IBM LUCJ circuits).
 
