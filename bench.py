@@ -49,7 +49,7 @@ TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tf32 : bf16 tensor throughpu
 # `--gemm-case 32768,1024,1024` mode of this script): dram read + write bytes and the case's
 # algorithmic flop.  Traffic grows with the rows processed, so a launch's traffic is scaled
 # by its flop.
-TC_CAPTURE_BYTES = 418.606848e6 + 244.045568e6
+TC_CAPTURE_BYTES = 401.568768e6 + 243.923456e6
 TC_CAPTURE_FLOP = 8.0 * 32768 * 1024 * 1024
 
 

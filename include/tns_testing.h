@@ -51,9 +51,10 @@ tns_status tns_test_cholw(int32_t batch, int32_t n, double shift, const double* 
 tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const float* A_dev, const float* B_dev, float* C_dev,
                            void* cuda_stream);
 
-/* Force the tensor-core GEMM's tile width for later launches: 128 or 256 real
- * columns, or 0 for the width the library's timing-based choice picks per shape
- * class (outputs of up to 64 complex columns always use 128). */
+/* Force the tensor-core GEMM's tile variant for later launches: 128 or 256 real
+ * columns with a pipelined ring of stages, 129 for 128 columns with one stage and
+ * three CTAs per SM, or 0 for the variant the library's timing-based choice picks per
+ * shape class (256 is taken as 128 for outputs of up to 64 complex columns). */
 tns_status tns_test_tc_tile(int32_t bn);
 
 /* The library's labelled tensor contraction C[c] = sum A[a] B[b] (einsum over the

@@ -145,6 +145,14 @@ static void free_state(tns_state* s) {
   if (s->gstream) cudaStreamDestroy(s->gstream);
   if (s->bp_host) cudaFreeHost(s->bp_host);
   s->bp_host = nullptr;
+  for (auto e : s->gate_events)
+    if (e) cudaEventDestroy(e);
+  s->gate_events.clear();
+  for (auto q : s->gate_streams)
+    if (q) cudaStreamDestroy(q);
+  s->gate_streams.clear();
+  if (s->gate_host) cudaFreeHost(s->gate_host);
+  s->gate_host = nullptr;
   for (auto* ec : {&s->env, &s->env_top})
     for (auto& E : ec->E)
       for (auto p : E.site)

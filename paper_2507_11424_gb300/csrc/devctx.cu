@@ -73,6 +73,9 @@ cudaError_t smem_optin(const void* fn, int bytes) {
   const auto key = std::make_tuple(ctx, fn, bytes);
   if (done.count(key)) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  // kernels that opt in use large shared-memory footprints: prefer the largest
+  // shared-memory carveout so that as many CTAs as fit can be resident per SM
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) done.insert(key);
   return e;
 }

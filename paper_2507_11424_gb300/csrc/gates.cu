@@ -6,6 +6,8 @@
 #include <cmath>
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "linalg.cuh"
@@ -154,18 +156,26 @@ static cudaError_t apply_leg(const cd* src, const int d[5], int leg, const cd* M
   return contract(A, B, C, Prec::F64, st);
 }
 
+// Buffers of one gate slot.  The gates of a layer are vertex-disjoint, so up to
+// GATE_SLOTS of them run at once, each on its own stream with its own buffers.
+constexpr int GATE_SLOTS = 8;
 struct GateBufs {
-  cd *t1, *t2, *G, *V, *Wm, *QA, *QB, *RA, *RB, *P, *theta, *U, *VV, *Us, *gm, *X[10], *Xi[10];
+  cd *t1, *t2, *G, *V, *Wm, *QA, *QB, *RA, *RB, *P, *theta, *U, *VV, *Us, *gm, *gA, *gB, *X[10], *Xi[10];
   double *lam, *sig;
   int* status;
+  cudaStream_t st;
+  int slot;
 };
 
-static tns_status gate_buffers(tns_state* s, GateBufs& b) {
+static tns_status gate_buffers(tns_state* s, GateBufs& b, int slot) {
   const long long chi = s->chi_max;
   long long tmax = 2;
   for (auto& c : s->cell) tmax = std::max(tmax, c.cap);
   const long long n = 2 * chi, m2 = 2 * n;  // R-factor rank and theta side
-  auto get = [&](const char* nm, size_t bytes, void** p) { return s->ws.get(nm, bytes, p); };
+  b.slot = slot;
+  auto get = [&](const char* nm, size_t bytes, void** p) {
+    return s->ws.get(std::string(nm) + "#" + std::to_string(slot), bytes, p);
+  };
   TNS_TRY_CUDA(get("g_t1", sizeof(cd) * tmax, (void**)&b.t1));
   TNS_TRY_CUDA(get("g_t2", sizeof(cd) * tmax, (void**)&b.t2));
   TNS_TRY_CUDA(get("g_G", sizeof(cd) * m2 * m2, (void**)&b.G));
@@ -184,6 +194,8 @@ static tns_status gate_buffers(tns_state* s, GateBufs& b) {
   TNS_TRY_CUDA(get("g_lam", sizeof(double) * m2, (void**)&b.lam));
   TNS_TRY_CUDA(get("g_sig", sizeof(double) * m2, (void**)&b.sig));
   TNS_TRY_CUDA(get("g_status", sizeof(int) * 64, (void**)&b.status));
+  TNS_TRY_CUDA(get("g_gA", sizeof(cd) * tmax, (void**)&b.gA));
+  TNS_TRY_CUDA(get("g_gB", sizeof(cd) * tmax, (void**)&b.gB));
   for (int i = 0; i < 10; ++i) {
     char nm[32];
     snprintf(nm, sizeof nm, "g_X%d", i);
@@ -194,19 +206,20 @@ static tns_status gate_buffers(tns_state* s, GateBufs& b) {
   return TNS_OK;
 }
 
-// work buffer for Jacobi problems that do not fit in shared memory
-static tns_status jacobi_work(tns_state* s, int m, int n, int batch, cd** w) {
+// work buffer (of the slot) for Jacobi problems that do not fit in shared memory
+static tns_status jacobi_work(tns_state* s, const GateBufs& b, int m, int n, int batch, cd** w) {
   *w = nullptr;
   if (jacobi_fits_smem(m, n)) return TNS_OK;
   long long np = n + (n & 1);
-  TNS_TRY_CUDA(s->ws.get("jac_work", sizeof(cd) * batch * ((long long)m * np + np * np + 2 * np * np), (void**)w));
+  TNS_TRY_CUDA(s->ws.get("jac_work#" + std::to_string(b.slot),
+                         sizeof(cd) * batch * ((long long)m * np + np * np + 2 * np * np), (void**)w));
   return TNS_OK;
 }
 
 // Gram-matrix orthonormalisation of the columns (s, j) of t viewed as
 // A[(others), (s, j)]: two passes of Q = A V Lambda^{-1/2}; R = Q^H A.
 static tns_status reduce_side(tns_state* s, GateBufs& b, const cd* t, const int d[5], int j, cd* Q, cd* R) {
-  cudaStream_t st = s->st;
+  cudaStream_t st = b.st;
   const int n = d[0] * d[j];
   std::string lab = "suldr";
   std::string others;
@@ -220,7 +233,7 @@ static tns_status reduce_side(tns_state* s, GateBufs& b, const cd* t, const int 
   TNS_TRY_CUDA(contract(view((void*)t, labA, dims5(d), true), view((void*)t, labB, dims5(d)),
                         view(b.G, std::string("SJ") + 's' + lab[j], {d[0], d[j], d[0], d[j]}), Prec::F64, st));
   cd* work = nullptr;
-  TNS_TRY(jacobi_work(s, n, n, 1, &work));
+  TNS_TRY(jacobi_work(s, b, n, n, 1, &work));
   TNS_TRY_CUDA(eigh_batched(b.G, (long long)n * n, n, n, 1, b.lam, b.V, (long long)n * n, work, b.status, st));
   gram_w_kernel<<<blocks((long long)n * n), 256, 0, st>>>(b.lam, b.V, n, 1e-30, b.Wm);
   s->launches += 2;
@@ -249,7 +262,7 @@ static tns_status reduce_side(tns_state* s, GateBufs& b, const cd* t, const int 
 // last step writes the cell's storage).  c.dim already holds the new bond k.
 static tns_status rebuild_side(tns_state* s, GateBufs& b, Cell& c, int j, int n, const cd* Q, const cd* Us,
                                const std::vector<int>& glegs, cd* const* Xi) {
-  cudaStream_t st = s->st;
+  cudaStream_t st = b.st;
   const std::string lab = "suldr";
   std::string others;
   std::vector<long long> qd;
@@ -278,7 +291,7 @@ static tns_status gauge_side(tns_state* s, GateBufs& b, const Cell& c, const std
   const cd* cur = c.t;
   for (size_t i = 0; i < glegs.size(); ++i) {
     cd* dst = (i + 1 == glegs.size()) ? out : bufs[i & 1];
-    TNS_TRY_CUDA(apply_leg(cur, c.dim, glegs[i], X[i], dst, s->st));
+    TNS_TRY_CUDA(apply_leg(cur, c.dim, glegs[i], X[i], dst, b.st));
     cur = dst;
   }
   *res = out;
@@ -292,9 +305,9 @@ static tns_status gauge_mats(tns_state* s, GateBufs& b, int ci, const std::vecto
     int D = s->cell[ci].dim[leg];
     const cd* m = s->msg[ci * 5 + leg];
     cd* work = nullptr;
-    TNS_TRY(jacobi_work(s, D, D, 1, &work));
-    TNS_TRY_CUDA(eigh_batched((cd*)m, (long long)D * D, D, D, 1, b.lam, b.V, (long long)D * D, work, b.status, s->st));
-    gauge_from_eig_kernel<<<blocks((long long)D * D), 256, 0, s->st>>>(b.lam, b.V, D, X[i], Xi[i]);
+    TNS_TRY(jacobi_work(s, b, D, D, 1, &work));
+    TNS_TRY_CUDA(eigh_batched((cd*)m, (long long)D * D, D, D, 1, b.lam, b.V, (long long)D * D, work, b.status, b.st));
+    gauge_from_eig_kernel<<<blocks((long long)D * D), 256, 0, b.st>>>(b.lam, b.V, D, X[i], Xi[i]);
     s->launches += 2;
   }
   return TNS_OK;
@@ -309,68 +322,120 @@ static int leg_between(const tns_state* s, int ca, int cb) {
   return -1;
 }
 
-static tns_status apply_2q(tns_state* s, GateBufs& b, int q0, int q1, const cd* gmat, int chi, double cutoff,
-                           double* eps_out) {
-  cudaStream_t st = s->st;
-  const int ca = s->qcell[q0], cb = s->qcell[q1];
-  const int j = leg_between(s, ca, cb);
-  const int jb = opp_leg(j);
-  Cell& A = s->cell[ca];
-  Cell& B = s->cell[cb];
+// A two-qubit gate in two halves.  gate_begin enqueues, on the slot's stream, the
+// gauging, the QR reduction of both sides, theta = G R_A R_B and its SVD, and copies
+// the singular values and the SVD status to the slot's pinned host block (event
+// recorded after the copy); it never waits.  gate_end waits for that event, picks the
+// kept rank and epsilon (Eq. 1) on the host, and enqueues the rebuild of both sides and
+// the bond messages.
+struct GateJob {
+  int q0, q1, ca, cb, j, jb, n, m2;
   std::vector<int> ga, gb;
+  double* h_sig;                 // pinned: m2 singular values, then the status word
+};
+
+static tns_status gate_begin(tns_state* s, GateBufs& b, GateJob& jb_, const cd* gmat, cudaEvent_t ev) {
+  cudaStream_t st = b.st;
+  jb_.ca = s->qcell[jb_.q0];
+  jb_.cb = s->qcell[jb_.q1];
+  jb_.j = leg_between(s, jb_.ca, jb_.cb);
+  jb_.jb = opp_leg(jb_.j);
+  Cell& A = s->cell[jb_.ca];
+  Cell& B = s->cell[jb_.cb];
+  jb_.ga.clear();
+  jb_.gb.clear();
   for (int leg = 1; leg <= 4; ++leg) {
-    if (leg != j && A.edge[leg]) ga.push_back(leg);
-    if (leg != jb && B.edge[leg]) gb.push_back(leg);
+    if (leg != jb_.j && A.edge[leg]) jb_.ga.push_back(leg);
+    if (leg != jb_.jb && B.edge[leg]) jb_.gb.push_back(leg);
   }
-  TNS_TRY(gauge_mats(s, b, ca, ga, b.X, b.Xi));
-  TNS_TRY(gauge_mats(s, b, cb, gb, b.X + 5, b.Xi + 5));
-  cd *gA = nullptr, *gB = nullptr;
-  TNS_TRY_CUDA(s->ws.get("g_gA", sizeof(cd) * A.cap, (void**)&gA));
-  TNS_TRY_CUDA(s->ws.get("g_gB", sizeof(cd) * B.cap, (void**)&gB));
+  TNS_TRY(gauge_mats(s, b, jb_.ca, jb_.ga, b.X, b.Xi));
+  TNS_TRY(gauge_mats(s, b, jb_.cb, jb_.gb, b.X + 5, b.Xi + 5));
   const cd *tA = nullptr, *tB = nullptr;
-  TNS_TRY(gauge_side(s, b, A, ga, b.X, gA, &tA));
-  TNS_TRY(gauge_side(s, b, B, gb, b.X + 5, gB, &tB));
-  const int Dj = A.dim[j];
+  TNS_TRY(gauge_side(s, b, A, jb_.ga, b.X, b.gA, &tA));
+  TNS_TRY(gauge_side(s, b, B, jb_.gb, b.X + 5, b.gB, &tB));
+  const int Dj = A.dim[jb_.j];
   const int n = A.dim[0] * Dj;  // = B.dim[0] * Dj
-  TNS_TRY(reduce_side(s, b, tA, A.dim, j, b.QA, b.RA));
-  TNS_TRY(reduce_side(s, b, tB, B.dim, jb, b.QB, b.RB));
+  jb_.n = n;
+  TNS_TRY(reduce_side(s, b, tA, A.dim, jb_.j, b.QA, b.RA));
+  TNS_TRY(reduce_side(s, b, tB, B.dim, jb_.jb, b.QB, b.RB));
   TNS_TRY_CUDA(contract(view(b.RA, "xsb", {n, 2, Dj}), view(b.RB, "ytb", {n, 2, Dj}), view(b.P, "xsyt", {n, 2, n, 2}),
                         Prec::F64, st));
   TNS_TRY_CUDA(contract(view((void*)gmat, "opst", {2, 2, 2, 2}), view(b.P, "xsyt", {n, 2, n, 2}),
                         view(b.theta, "xoyp", {n, 2, n, 2}), Prec::F64, st));
   const int m2 = 2 * n;
+  jb_.m2 = m2;
   cd* work = nullptr;
-  TNS_TRY(jacobi_work(s, m2, m2, 1, &work));
+  TNS_TRY(jacobi_work(s, b, m2, m2, 1, &work));
   TNS_TRY_CUDA(svd_batched(b.theta, (long long)m2 * m2, m2, m2, m2, 1, b.sig, b.U, (long long)m2 * m2, b.VV,
                            (long long)m2 * m2, work, b.status, st));
   s->launches += 1;
-  std::vector<double> sig(m2);
+  TNS_TRY_CUDA(cudaMemcpyAsync(jb_.h_sig, b.sig, sizeof(double) * m2, cudaMemcpyDeviceToHost, st));
+  TNS_TRY_CUDA(cudaMemcpyAsync(jb_.h_sig + m2, b.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TNS_TRY_CUDA(cudaEventRecord(ev, st));
+  return TNS_OK;
+}
+
+static tns_status gate_end(tns_state* s, GateBufs& b, GateJob& jb_, cudaEvent_t ev, int chi, double cutoff,
+                           double* eps_out) {
+  cudaStream_t st = b.st;
+  TNS_TRY_CUDA(cudaEventSynchronize(ev));
+  const int m2 = jb_.m2, n = jb_.n;
+  const double* sig = jb_.h_sig;
   int status = 0;
-  TNS_TRY_CUDA(cudaMemcpyAsync(sig.data(), b.sig, sizeof(double) * m2, cudaMemcpyDeviceToHost, st));
-  TNS_TRY_CUDA(cudaMemcpyAsync(&status, b.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TNS_TRY_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(&status, jb_.h_sig + m2, sizeof(int));
   double tot = 0.0;
-  for (double x : sig) tot += x * x;
-  if (!std::isfinite(tot)) { set_error("non-finite singular values in gate on qubits %d,%d", q0, q1); return TNS_ERR_NUMERIC; }
+  for (int i = 0; i < m2; ++i) tot += sig[i] * sig[i];
+  if (!std::isfinite(tot)) {
+    set_error("non-finite singular values in gate on qubits %d,%d", jb_.q0, jb_.q1);
+    return TNS_ERR_NUMERIC;
+  }
   int keep = 0;
-  for (double x : sig)
-    if (sig[0] > 0 && x > cutoff * sig[0]) ++keep;
+  for (int i = 0; i < m2; ++i)
+    if (sig[0] > 0 && sig[i] > cutoff * sig[0]) ++keep;
   int k = std::max(1, std::min(chi, keep));
   double disc = 0.0;
   for (int i = k; i < m2; ++i) disc += sig[i] * sig[i];
   double eps = tot > 0.0 ? disc / tot : 0.0;
+  Cell& A = s->cell[jb_.ca];
+  Cell& B = s->cell[jb_.cb];
   // side A
   scale_cols_kernel<<<blocks((long long)m2 * k), 256, 0, st>>>(b.U, m2, m2, k, b.sig, 0, b.Us);
-  A.dim[j] = k;
-  TNS_TRY(rebuild_side(s, b, A, j, n, b.QA, b.Us, ga, b.Xi));
+  A.dim[jb_.j] = k;
+  TNS_TRY(rebuild_side(s, b, A, jb_.j, n, b.QA, b.Us, jb_.ga, b.Xi));
   scale_cols_kernel<<<blocks((long long)m2 * k), 256, 0, st>>>(b.VV, m2, m2, k, b.sig, 1, b.Us);
-  B.dim[jb] = k;
-  TNS_TRY(rebuild_side(s, b, B, jb, n, b.QB, b.Us, gb, b.Xi + 5));
-  diag_msg_kernel<<<1, 256, 0, st>>>(b.sig, k, s->msg[ca * 5 + j], s->msg[cb * 5 + jb]);
+  B.dim[jb_.jb] = k;
+  TNS_TRY(rebuild_side(s, b, B, jb_.jb, n, b.QB, b.Us, jb_.gb, b.Xi + 5));
+  diag_msg_kernel<<<1, 256, 0, st>>>(b.sig, k, s->msg[jb_.ca * 5 + jb_.j], s->msg[jb_.cb * 5 + jb_.jb]);
   s->launches += 3;
   s->log_f += (eps < 1.0) ? std::log1p(-eps) : -INFINITY;
   if (eps_out) *eps_out = eps;
-  if (status != 0) { set_error("SVD sweep cap reached in gate on qubits %d,%d", q0, q1); return TNS_ERR_NUMERIC; }
+  if (status != 0) {
+    set_error("SVD sweep cap reached in gate on qubits %d,%d", jb_.q0, jb_.q1);
+    return TNS_ERR_NUMERIC;
+  }
+  return TNS_OK;
+}
+
+// GATE_SLOTS streams, their events and the pinned host blocks, created on first use.
+static tns_status gate_slots(tns_state* s) {
+  const size_t per = (size_t)4 * s->chi_max + 2;
+  if ((int)s->gate_streams.size() < GATE_SLOTS) {
+    for (int i = (int)s->gate_streams.size(); i < GATE_SLOTS; ++i) {
+      cudaStream_t q = nullptr;
+      cudaEvent_t e = nullptr;
+      TNS_TRY_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+      s->gate_streams.push_back(q);
+      TNS_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      s->gate_events.push_back(e);
+    }
+  }
+  if (s->gate_host_n < per * GATE_SLOTS) {
+    if (s->gate_host) cudaFreeHost(s->gate_host);
+    s->gate_host = nullptr;
+    s->gate_host_n = 0;
+    TNS_TRY_CUDA(cudaMallocHost((void**)&s->gate_host, sizeof(double) * per * GATE_SLOTS));
+    s->gate_host_n = per * GATE_SLOTS;
+  }
   return TNS_OK;
 }
 
@@ -400,27 +465,72 @@ tns_status apply_gate_layer(tns_state* s, int n_gates, const int32_t* sites, con
       if (!std::isfinite(mats[32 * g + i])) { set_error("gate %d has non-finite entries", g); return TNS_ERR_ARG; }
   }
   if (n_gates == 0) return TNS_OK;
-  GateBufs b;
-  TNS_TRY(gate_buffers(s, b));
+  TNS_TRY(gate_slots(s));
+  GateBufs bufs[GATE_SLOTS];
+  for (int i = 0; i < GATE_SLOTS; ++i) {
+    TNS_TRY(gate_buffers(s, bufs[i], i));
+    bufs[i].st = s->gate_streams[i];
+  }
   cd* gm = nullptr;
   TNS_TRY_CUDA(s->ws.get("g_gates", sizeof(cd) * 16 * n_gates, (void**)&gm));
   TNS_TRY_CUDA(cudaMemcpyAsync(gm, mats, sizeof(cd) * 16 * n_gates, cudaMemcpyHostToDevice, s->st));
+  // the slots start after everything already on the state's stream (the gate
+  // matrices, earlier layers, BP) and the state's stream waits for all slots at the end
+  cudaEvent_t fork = nullptr;
+  TNS_TRY_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t e;
+    ~EvGuard() { if (e) cudaEventDestroy(e); }
+  } fork_guard{fork};
+  TNS_TRY_CUDA(cudaEventRecord(fork, s->st));
+  for (int i = 0; i < GATE_SLOTS; ++i) TNS_TRY_CUDA(cudaStreamWaitEvent(bufs[i].st, fork, 0));
+  const size_t per = (size_t)4 * s->chi_max + 2;
   tns_status result = TNS_OK;
-  for (int g = 0; g < n_gates; ++g) {
-    int a = sites[2 * g], bq = sites[2 * g + 1];
-    double eps = 0.0;
-    if (bq < 0) {
-      Cell& c = s->cell[s->qcell[a]];
-      TNS_TRY_CUDA(contract(view(gm + 16 * g, "os", {2, 2}), view(c.t, "suldr", dims5(c.dim)),
-                            view(b.t1, "ouldr", dims5(c.dim)), Prec::F64, s->st));
-      TNS_TRY_CUDA(cudaMemcpyAsync(c.t, b.t1, sizeof(cd) * c.size(), cudaMemcpyDeviceToDevice, s->st));
-    } else {
-      tns_status r = apply_2q(s, b, a, bq, gm + 16 * g, chi, cutoff, &eps);
-      if (r == TNS_ERR_NUMERIC) result = r;
-      else if (r != TNS_OK) return r;
+  auto join = [&]() -> tns_status {
+    for (int i = 0; i < GATE_SLOTS; ++i) {
+      TNS_TRY_CUDA(cudaEventRecord(s->gate_events[i], bufs[i].st));
+      TNS_TRY_CUDA(cudaStreamWaitEvent(s->st, s->gate_events[i], 0));
     }
-    if (eps_out) eps_out[g] = eps;
+    return TNS_OK;
+  };
+  // gates in rounds of GATE_SLOTS: every gate's first half is enqueued (they overlap on
+  // the GPU), then the second halves in gate order as their singular values arrive
+  std::vector<GateJob> jobs(GATE_SLOTS);
+  for (int g0 = 0; g0 < n_gates; g0 += GATE_SLOTS) {
+    const int g1 = std::min(n_gates, g0 + GATE_SLOTS);
+    for (int g = g0; g < g1; ++g) {
+      const int slot = g - g0;
+      GateBufs& b = bufs[slot];
+      int a = sites[2 * g], bq = sites[2 * g + 1];
+      if (bq < 0) {
+        Cell& c = s->cell[s->qcell[a]];
+        tns_status r = TNS_OK;
+        cudaError_t e = contract(view(gm + 16 * g, "os", {2, 2}), view(c.t, "suldr", dims5(c.dim)),
+                                 view(b.t1, "ouldr", dims5(c.dim)), Prec::F64, b.st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.t, b.t1, sizeof(cd) * c.size(), cudaMemcpyDeviceToDevice, b.st);
+        if (e != cudaSuccess) r = cuda_status(e, "one-qubit gate");
+        if (r != TNS_OK) { join(); return r; }
+        continue;
+      }
+      GateJob& jb_ = jobs[slot];
+      jb_.q0 = a;
+      jb_.q1 = bq;
+      jb_.h_sig = s->gate_host + per * slot;
+      tns_status r = gate_begin(s, b, jb_, gm + 16 * g, s->gate_events[slot]);
+      if (r != TNS_OK) { join(); return r; }
+    }
+    for (int g = g0; g < g1; ++g) {
+      const int slot = g - g0;
+      double eps = 0.0;
+      if (sites[2 * g + 1] >= 0) {
+        tns_status r = gate_end(s, bufs[slot], jobs[slot], s->gate_events[slot], chi, cutoff, &eps);
+        if (r == TNS_ERR_NUMERIC) result = r;
+        else if (r != TNS_OK) { join(); return r; }
+      }
+      if (eps_out) eps_out[g] = eps;
+    }
   }
+  TNS_TRY(join());
   s->version++;
   TNS_TRY_CUDA(cudaStreamSynchronize(s->st));
   return result;

@@ -76,47 +76,57 @@ template <typename C> __global__ void take_cols_kernel(const cd* UB, int n, int 
 
 // Column phase convention: make sum_i K[i][col] / sqrt(i+1) real positive; when
 // that sum is below 1e-8, make the first largest-magnitude entry real positive.
-template <typename C> __global__ void phase_fix_kernel(C* K, int M, int Rk) {
+// Block (g, b) handles columns 32g .. 32g+31 of batch entry b: lane = column, warp =
+// row group (rows w, w + PF_GROUPS, ...), so every warp load is one coalesced run of
+// 32 consecutive columns of a row; the row groups' partial sums are combined in a
+// fixed order, then the same walk applies the phase.
+constexpr int PF_GROUPS = 16;
+template <typename C> __global__ void __launch_bounds__(32 * PF_GROUPS) phase_fix_kernel(C* K, int M, int Rk) {
   const long long b = blockIdx.y;
-  const int col = blockIdx.x;
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool active = col < Rk;
   C* k = K + b * (long long)M * Rk + col;
-  __shared__ double sx[128], sy[128], sm[128];
-  __shared__ int si[128];
+  __shared__ double sx[PF_GROUPS][32], sy[PF_GROUPS][32], sm[PF_GROUPS][32];
+  __shared__ int si[PF_GROUPS][32];
+  __shared__ cd ph[32];
   double cx = 0.0, cy = 0.0, best = -1.0;
   int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    cd v = to_cd(k[(long long)i * Rk]);
-    double w = 1.0 / sqrt((double)i + 1.0);
-    cx += w * v.x;
-    cy += w * v.y;
-    double a = cabs2(v);
-    if (a > best) { best = a; bi = i; }
-  }
-  sx[threadIdx.x] = cx; sy[threadIdx.x] = cy; sm[threadIdx.x] = best; si[threadIdx.x] = bi;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      sx[threadIdx.x] += sx[threadIdx.x + o];
-      sy[threadIdx.x] += sy[threadIdx.x + o];
-      double m2 = sm[threadIdx.x + o];
-      int i2 = si[threadIdx.x + o];
-      if (m2 > sm[threadIdx.x] || (m2 == sm[threadIdx.x] && i2 < si[threadIdx.x])) { sm[threadIdx.x] = m2; si[threadIdx.x] = i2; }
+  if (active)
+    for (int i = grp; i < M; i += PF_GROUPS) {
+      cd v = to_cd(k[(long long)i * Rk]);
+      double w = 1.0 / sqrt((double)i + 1.0);
+      cx += w * v.x;
+      cy += w * v.y;
+      double a = cabs2(v);
+      if (a > best) { best = a; bi = i; }       // rows ascend: the first largest wins ties
     }
-    __syncthreads();
-  }
-  __shared__ cd ph;
-  if (threadIdx.x == 0) {
-    double ax = sx[0], ay = sy[0], a = sqrt(ax * ax + ay * ay);
-    if (a > 1e-8) ph = mk(ax / a, -ay / a);
-    else if (sm[0] > 0.0 && si[0] < M) {
-      cd v = to_cd(k[(long long)si[0] * Rk]);
+  sx[grp][lane] = cx; sy[grp][lane] = cy; sm[grp][lane] = best; si[grp][lane] = bi;
+  __syncthreads();
+  if (grp == 0 && active) {
+    double ax = 0.0, ay = 0.0, m = -1.0;
+    int mi = 0x7fffffff;
+    for (int g = 0; g < PF_GROUPS; ++g) {
+      ax += sx[g][lane];
+      ay += sy[g][lane];
+      const double m2 = sm[g][lane];
+      const int i2 = si[g][lane];
+      if (m2 > m || (m2 == m && i2 < mi)) { m = m2; mi = i2; }
+    }
+    const double a = sqrt(ax * ax + ay * ay);
+    cd p = mk(1.0, 0.0);
+    if (a > 1e-8) p = mk(ax / a, -ay / a);
+    else if (m > 0.0 && mi < M) {
+      cd v = to_cd(k[(long long)mi * Rk]);
       double av = sqrt(cabs2(v));
-      ph = mk(v.x / av, -v.y / av);
-    } else ph = mk(1.0, 0.0);
+      p = mk(v.x / av, -v.y / av);
+    }
+    ph[lane] = p;
   }
   __syncthreads();
-  cd p = ph;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+  if (!active) return;
+  const cd p = ph[lane];
+  for (int i = grp; i < M; i += PF_GROUPS) {
     cd v = to_cd(k[(long long)i * Rk]);
     k[(long long)i * Rk] = from_cd<C>(cmul(v, p));
   }
@@ -140,21 +150,35 @@ template <typename C> __global__ void normalize_last_kernel(const C* T, long lon
   if (threadIdx.x == 0 && logscale) logscale[b] += nrm > 0.0 ? log(nrm) : -INFINITY;
 }
 
-// Scale each batch entry of F to unit Frobenius norm (conditionals are scale free).
-template <typename C> __global__ void normalize_kernel(C* F, long long n) {
-  const long long b = blockIdx.x;
+// Scale each batch entry of F to unit Frobenius norm (conditionals are scale free),
+// in two kernels with NRM_SPLIT blocks per batch entry: norm_partial_kernel sums
+// |F|^2 over its slice into part[b][k]; normalize_apply_kernel adds the NRM_SPLIT
+// partials in index order (the same total in every block) and scales its slice.
+constexpr int NRM_SPLIT = 16;
+template <typename C> __global__ void norm_partial_kernel(const C* F, long long n, double* part) {
+  const long long b = blockIdx.y;
+  const long long chunk = (n + NRM_SPLIT - 1) / NRM_SPLIT;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
   __shared__ double red[256];
   double s2 = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) s2 += cabs2(to_cd(F[b * n + i]));
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s2 += cabs2(to_cd(F[b * n + i]));
   red[threadIdx.x] = s2;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  double nrm = sqrt(red[0]);
-  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) F[b * n + i] = from_cd<C>(cscale(to_cd(F[b * n + i]), inv));
+  if (threadIdx.x == 0) part[b * NRM_SPLIT + blockIdx.x] = red[0];
+}
+template <typename C> __global__ void normalize_apply_kernel(C* F, long long n, const double* part) {
+  const long long b = blockIdx.y;
+  const long long chunk = (n + NRM_SPLIT - 1) / NRM_SPLIT;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double s2 = 0.0;
+  for (int k = 0; k < NRM_SPLIT; ++k) s2 += part[b * NRM_SPLIT + k];
+  const double nrm = sqrt(s2);
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) F[b * n + i] = from_cd<C>(cscale(to_cd(F[b * n + i]), inv));
 }
 
 // Per-call arguments of the sampler's chunk, read on the device so that one captured
@@ -714,7 +738,7 @@ static tns_status truncate(Ctx& cx, void* T, long long S, long long M, long long
                          view(Kout, "Smr", {S, M, Rk}), cx.gp));
   dispatch(cx.f64, [&](auto* tp) {
     using C = std::remove_pointer_t<decltype(tp)>;
-    phase_fix_kernel<C><<<dim3(Rk, (unsigned)S), 128, 0, cx.st>>>((C*)Kout, (int)M, Rk);
+    phase_fix_kernel<C><<<dim3((Rk + 31) / 32, (unsigned)S), 32 * PF_GROUPS, 0, cx.st>>>((C*)Kout, (int)M, Rk);
   });
   // C = K^H T, stored conjugate-transposed: Cout[S][n][r] = conj(C[r][n]) = (T^H K)[n][r]
   TNS_TRY_CUDA(pcontract(s, PC_ZIP, view(Th, "Snm", {S, N, M}), view(Kout, "Smr", {S, M, Rk}),
@@ -1111,11 +1135,15 @@ tns_status sample(tns_state* s, int chi_b, long long n, uint64_t seed, const uin
         // R3: F_j[S][a][e][c] = sum_{s,B,D} T2 conj K'[c,s,D,B]
         TNS_TRY_CUDA(pcontract(s, PC_SWEEP, view(bigB, "SaesBD", {Sz, ka, re, P, kb, Dd}), Kview(j, 'c', 's', 'D', 'B', Sz, true),
                               view(Fs[j], "Saec", {Sz, ka, re, ka}), cx.gp));
+        double* nrm_part = nullptr;
+        TNS_TRY(wsget(s, "z_nrm", sizeof(double) * Sz * NRM_SPLIT, (void**)&nrm_part));
         dispatch(cx.f64, [&](auto* tp) {
           using C = std::remove_pointer_t<decltype(tp)>;
-          normalize_kernel<C><<<(unsigned)Sz, 256, 0, cx.st>>>((C*)Fs[j], ka * re * ka);
+          const dim3 g(NRM_SPLIT, (unsigned)Sz);
+          norm_partial_kernel<C><<<g, 256, 0, cx.st>>>((const C*)Fs[j], ka * re * ka, nrm_part);
+          normalize_apply_kernel<C><<<g, 256, 0, cx.st>>>((C*)Fs[j], ka * re * ka, nrm_part);
         });
-        s->launches++;
+        s->launches += 2;
         fdim[j] = re;
       }
       // left sweep: draw the row's qubits

@@ -112,6 +112,12 @@ struct tns_state {
   cudaStream_t gstream = nullptr;       // private stream that graphs are captured and replayed on
   cudaEvent_t gev[2] = {nullptr, nullptr};
   long long work_version = -1;
+  // gate layers: the gates of a group run concurrently on these streams (one slot per
+  // stream: its own buffers, a pinned host block for the singular values, an event)
+  std::vector<cudaStream_t> gate_streams;
+  std::vector<cudaEvent_t> gate_events;
+  double* gate_host = nullptr;          // [slots][4 chi_max + 1] singular values + status
+  size_t gate_host_n = 0;
   // pinned host buffer for BP's per-message residuals (two iterations in flight)
   double* bp_host = nullptr;
   size_t bp_host_n = 0;

@@ -41,14 +41,17 @@ namespace tns {
 namespace {
 constexpr int BM = 128, BKF = 32;
 constexpr size_t TILE_A = (size_t)BM * BKF * sizeof(float);   // 16 KB
-// pipeline depth: each stage holds A, A_lo, B_hi, B_lo (96 KB at BN = 256, 64 KB at BN = 128)
-template <int BN> struct Stages { static constexpr int value = BN == 256 ? 2 : 3; };
+// pipeline depth: each stage holds A, A_lo, B_hi, B_lo (96 KB at BN = 256, 64 KB at BN = 128).
+// Variants (BN, STAGES, CTAs per SM): (256, 2, 1) and (128, 3, 1) pipeline TMA and MMA
+// within a CTA; (128, 1, 3) keeps one stage per CTA and three CTAs per SM, so one
+// CTA's epilogue and loads overlap the others' MMAs (short-K contractions, whose
+// tiles are mostly set-up and epilogue).
 // warps: 0 = TMA producer (thread 0), 1 = MMA issuer (thread 32), 2..2+CONV_WARPS-1 =
 // converters; warps 0-3 also run the epilogue (TMEM lane quarter = warp index)
 constexpr int CONV_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * CONV_WARPS;
-template <int BN> constexpr size_t smem_bytes() {
-  return Stages<BN>::value * (2 * TILE_A + 2 * (size_t)BN * BKF * sizeof(float)) + 1024 + 256;
+template <int BN, int STAGES> constexpr size_t smem_bytes() {
+  return STAGES * (2 * TILE_A + 2 * (size_t)BN * BKF * sizeof(float)) + 1024 + 256;
 }
 constexpr unsigned long long WAIT_NS = 1000000000ull;          // 1 s
 
@@ -93,11 +96,10 @@ __device__ __forceinline__ long long tc_batch_off(const TcEpilogue& e, long long
   return o;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int BN, int STAGES, int MINB>
+__global__ void __launch_bounds__(TC_THREADS, MINB)
 tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBhi,
                       const __grid_constant__ CUtensorMap mBlo, const TcArgs p) {
-  constexpr int STAGES = Stages<BN>::value;
   constexpr size_t TILE_B = (size_t)BN * BKF * sizeof(float);
   constexpr int NC = BN / 2;                       // complex columns per tile
   extern __shared__ unsigned char smem_raw[];
@@ -329,8 +331,9 @@ static bool make_map(CUtensorMap* map, const float* ptr, long long rows, long lo
 
 bool tc_available() { return encode_fn() != nullptr; }
 
-template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArgs& a0, cudaStream_t st) {
-  constexpr size_t SMEM = smem_bytes<BN>();
+template <int BN, int STAGES, int MINB>
+static cudaError_t launch_variant(const TcOperands& op, const TcArgs& a0, cudaStream_t st) {
+  constexpr size_t SMEM = smem_bytes<BN, STAGES>();
   TcArgs a = a0;
   const long long rowsA = (a.a_batched ? a.nbatch : 1) * a.e.M;
   const long long rowsB = (a.b_batched ? a.nbatch : 1) * 2LL * a.e.N;
@@ -343,7 +346,7 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
       !make_map(&mblo, op.Blo, rowsB, a.Kr, op.ldb, BN))
     return cudaErrorInvalidValue;
   {
-    cudaError_t e = smem_optin((const void*)tc_gemm_tf32x3_kernel<BN>, (int)SMEM);
+    cudaError_t e = smem_optin((const void*)tc_gemm_tf32x3_kernel<BN, STAGES, MINB>, (int)SMEM);
     if (e != cudaSuccess) return e;
   }
   a.tiles_n = (int)((2LL * a.e.N + BN - 1) / BN);
@@ -353,21 +356,29 @@ template <int BN> static cudaError_t launch_bn(const TcOperands& op, const TcArg
   a.tiles_m = (int)tm;
   const long long tiles = tm * a.tiles_n * (a.merged ? 1 : a.nbatch);
   if (tiles >= (1LL << 31)) return cudaErrorNotSupported;
-  tc_gemm_tf32x3_kernel<BN><<<(unsigned)tiles, TC_THREADS, SMEM, st>>>(ma, mbhi, mblo, a);
+  tc_gemm_tf32x3_kernel<BN, STAGES, MINB><<<(unsigned)tiles, TC_THREADS, SMEM, st>>>(ma, mbhi, mblo, a);
   return cudaGetLastError();
 }
 
-// Tile width per shape class.  Outputs of up to 64 complex columns always take the
-// 128-column tile (a 256-column tile would be mostly padding).  Wider outputs take
-// whichever of 128 and 256 ran faster the first time the class was met: both widths
-// are launched once, timed with CUDA events on the caller's stream, and the choice is
-// frozen for the rest of the process.  Each output element accumulates the same MMA
-// sequence over K under either width, so the choice changes speed only (a test holds
-// the two bit-identical).  During stream capture an untuned class takes the 256 tile.
+// variant codes: 256 = (256, 2, 1), 128 = (128, 3, 1), TC_TILE_128_SINGLE = (128, 1, 3)
+static cudaError_t launch_code(int code, const TcOperands& op, const TcArgs& a, cudaStream_t st) {
+  if (code == 256) return launch_variant<256, 2, 1>(op, a, st);
+  if (code == TC_TILE_128_SINGLE) return launch_variant<128, 1, 3>(op, a, st);
+  return launch_variant<128, 3, 1>(op, a, st);
+}
+
+// Tile variant per shape class.  Candidates: the 128-column tile, pipelined or
+// single-stage with three CTAs per SM, and, for outputs wider than 64 complex columns,
+// the 256-column tile (narrower outputs would be mostly padding in it).  The first time
+// a class is met every candidate is launched once, timed with CUDA events on the
+// caller's stream, and the fastest is frozen for the rest of the process.  Each output
+// element accumulates the same MMA sequence over K under every variant, so the choice
+// changes speed only (a test holds the variants bit-identical).  During stream capture
+// an untuned class takes the pipelined tile of its width.
 namespace {
 std::mutex g_tile_mu;
 std::map<std::vector<long long>, int> g_tile;
-int g_force_bn = 0;                       // testing: 128 or 256 forces the width
+int g_force_bn = 0;                       // testing: forces a variant code
 }
 
 void tc_force_tile(int bn) {
@@ -377,12 +388,13 @@ void tc_force_tile(int bn) {
 
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st) {
   if (!tc_available() || a.e.M < 1 || a.e.N < 1 || a.Kr < 1 || a.nbatch < 1) return cudaErrorNotSupported;
-  if (tc_tile_n(a.e.N) == 128) return launch_bn<128>(op, a, st);
+  const bool narrow = tc_tile_n(a.e.N) == 128;
   int forced = 0;
   std::vector<long long> key;
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     forced = g_force_bn;
+    if (forced == 256 && narrow) forced = 128;
     if (!forced) {
       // class: row count to a power of two, exact N and K, operand sharing and batching
       const long long rows = a.merged ? a.nbatch * a.e.M : a.e.M;
@@ -393,27 +405,35 @@ cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t s
       if (it != g_tile.end()) forced = it->second;
     }
   }
-  if (forced == 128) return launch_bn<128>(op, a, st);
-  if (forced == 256) return launch_bn<256>(op, a, st);
+  if (forced) return launch_code(forced, op, a, st);
+  const int fallback = narrow ? 128 : 256;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-    return launch_bn<256>(op, a, st);
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  for (auto& e : ev)
-    if (cudaEventCreate(&e) != cudaSuccess) return launch_bn<256>(op, a, st);
-  cudaError_t e = cudaEventRecord(ev[0], st);
-  if (e == cudaSuccess) e = launch_bn<128>(op, a, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-  if (e == cudaSuccess) e = launch_bn<256>(op, a, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-  if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-  float t128 = 0.f, t256 = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&t128, ev[0], ev[1]);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&t256, ev[1], ev[2]);
-  for (auto& x : ev) cudaEventDestroy(x);
+    return launch_code(fallback, op, a, st);
+  std::vector<int> cand = {128, TC_TILE_128_SINGLE};
+  if (!narrow) cand.push_back(256);
+  std::vector<cudaEvent_t> ev(cand.size() + 1, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+    e = launch_code(cand[i], op, a, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[i + 1], st);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+  int best = fallback;
+  float best_ms = 1e30f;
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    if (e == cudaSuccess && ms < best_ms) { best_ms = ms; best = cand[i]; }
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_tile_mu);
-  g_tile.emplace(key, t128 < t256 ? 128 : 256);
+  g_tile.emplace(key, best);
   return cudaSuccess;
 }
 

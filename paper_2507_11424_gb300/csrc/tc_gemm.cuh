@@ -71,6 +71,9 @@ bool tma_map_2d(CUtensorMap* map, bool bf16, const void* ptr, long long rows, lo
 // cudaErrorNotSupported when the shape or alignment does not fit the kernel.
 cudaError_t tc_gemm_tf32x3(const TcOperands& op, const TcArgs& a, cudaStream_t st);
 // Testing: force the tile width of later launches (128 or 256; 0 = the tuned choice).
+// Testing: force the tile variant of later launches (128, 256 or TC_TILE_128_SINGLE;
+// 0 = the timing-based choice).
+constexpr int TC_TILE_128_SINGLE = 129;
 void tc_force_tile(int bn);
 // Per-device error flag shared by every tensor-core launch (lazily allocated).
 int* tc_error_flag();

@@ -151,7 +151,10 @@ extern "C" tns_status tns_test_tcgemm(int64_t M, int32_t N, int32_t K, const flo
 }
 
 extern "C" tns_status tns_test_tc_tile(int32_t bn) {
-  if (bn != 0 && bn != 128 && bn != 256) { set_error("tile width must be 0, 128 or 256"); return TNS_ERR_ARG; }
+  if (bn != 0 && bn != 128 && bn != 256 && bn != TC_TILE_128_SINGLE) {
+    set_error("tile variant must be 0, 128, 129 or 256");
+    return TNS_ERR_ARG;
+  }
   tc_force_tile(bn);
   return TNS_OK;
 }

@@ -1,15 +1,23 @@
-"""Write the oracle's full-size reference draws for the 10x10 workload.
+"""Write the oracle's full-size reference draws for the 10x10 workload shape.
 
-Calls only ``oracle/`` and ``workloads/``.  The state is the 10x10 square-lattice
-domain-wall Heisenberg quench (7 Trotter layers, dt = 0.2) built by the oracle's
-BP-gauged simple update at chi = 16, with a fixed number of BP sweeps after every
-gate group (``BP_SWEEPS``; the GPU test rebuilds the same state with the same
-function, ``build_state``).  The oracle then samples it at boundary rank
+Calls only ``oracle/`` and ``workloads/``.  The state is a 10x10 square-lattice
+domain-wall Heisenberg quench (7 Trotter layers, dt = 0.2) with one coupling per
+bond drawn from U[0.8, 1.2] (``workloads.disordered_heisenberg_circuit``, seed
+``J_SEED``), built by the oracle's BP-gauged simple update at chi = 16 with a fixed
+number of BP sweeps after every gate group (``BP_SWEEPS``; the GPU test rebuilds the
+same state with the same function, ``build_state``).  The couplings are disordered
+because the uniform quench's truncations meet exactly degenerate singular values
+(its lattice symmetries), where the kept basis, and hence the whole later state,
+depends on the rounding of the host's LAPACK: a 1e-13 change of the gates moves its
+per-gate truncation errors by 2e-6, so a state rebuilt on another machine is not the
+state the reference was computed on.  With disordered couplings the same change moves
+them by 7e-15.  The shapes (bond dimensions 16, boundary rank 64) and the launch
+configuration are those of the uniform workload.  The oracle then samples it at boundary rank
 chi_b = 64 with every truncation an exact truncated SVD (``exact=True``: the
 plain definition of the compressor, Methods and Appendix "Sampling from a Tensor
 Network State"), norm environments included, and stores per sample the drawn
 bits, q(x_q = 0 | prefix) for every qubit, and log q(x).  Output:
-``sq10x10_chib64_exact.npz`` next to this file (a few tens of KB).
+``sq10x10_disordered_chib64_exact.npz`` next to this file (a few tens of KB).
 
     python tests/golden/make_sq10x10_exact.py [n_samples] [--save-envs PATH]
 
@@ -37,7 +45,8 @@ from oracle.tns import GridTNS  # noqa: E402
 
 BP_SWEEPS = 4
 SEED = 20250711
-OUT = os.path.join(HERE, "sq10x10_chib64_exact.npz")
+J_SEED = 2507
+OUT = os.path.join(HERE, "sq10x10_disordered_chib64_exact.npz")
 
 
 def build_state():
@@ -47,7 +56,7 @@ def build_state():
     lat = w.make_lattice(cfg["lattice"])
     bits = w.domain_wall_bits(lat)
     t = GridTNS(lat.grid_rc, lat.edges, bits)
-    for g in w.heisenberg_circuit(lat, cfg["layers"], cfg["dt"]):
+    for g in w.disordered_heisenberg_circuit(lat, cfg["layers"], cfg["dt"], seed=J_SEED):
         t.apply_group(g, cfg["chi"])
         t.bp(BP_SWEEPS, 1e-10)
     return t, cfg, bits
@@ -75,7 +84,7 @@ def main():
         bits[i], logq[i], q0[i] = b[0], lq[0], q[0]
         print(f"sample {i} {time.time() - t0:.0f} s", flush=True)
         np.savez(OUT, bits=bits[: i + 1], q0=q0[: i + 1], logq=logq[: i + 1], log_norm=log_norm,
-                 log_fidelity=t.log_fidelity, seed=SEED, chi_b=R, bp_sweeps=BP_SWEEPS,
+                 log_fidelity=t.log_fidelity, seed=SEED, chi_b=R, bp_sweeps=BP_SWEEPS, j_seed=J_SEED,
                  sector=int(bits0.sum()))
 
 

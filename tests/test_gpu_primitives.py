@@ -222,8 +222,9 @@ def test_device_contraction_planner(env, case):
 
 
 def test_tile_widths_are_bit_identical(env):
-    """Both tensor-core tile widths (128 and 256 real columns) give the same bits, so
-    the library's timing-based choice between them never changes a result."""
+    """Every tensor-core tile variant (128 and 256 real columns pipelined, 128 columns
+    single-stage with three CTAs per SM) gives the same bits, so the library's
+    timing-based choice between them never changes a result."""
     import ctypes as C
     torch, lib = env
     rng = np.random.default_rng(21)
@@ -233,7 +234,7 @@ def test_tile_widths_are_bit_identical(env):
         dA = torch.tensor(A.view(np.float32), device="cuda")
         dB = torch.tensor(B.view(np.float32), device="cuda")
         out = []
-        for bn in (128, 256):
+        for bn in (128, 256, 129):
             assert lib.tns_test_tc_tile(bn) == 0
             dC = torch.full((M, 2 * N), float("nan"), device="cuda")
             assert lib.tns_test_tcgemm(M, N, K, C.c_void_p(dA.data_ptr()), C.c_void_p(dB.data_ptr()),
@@ -241,3 +242,4 @@ def test_tile_widths_are_bit_identical(env):
             out.append(dC.cpu())
         assert lib.tns_test_tc_tile(0) == 0
         assert torch.equal(out[0], out[1])
+        assert torch.equal(out[0], out[2])

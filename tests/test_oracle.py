@@ -51,6 +51,32 @@ def test_heisenberg_gate_closed_form(dt):
     assert np.abs(U.conj().T @ U - np.eye(4)).max() < 1e-14
 
 
+def test_disordered_heisenberg_circuit():
+    """One coupling per bond in [0.8, 1.2], every gate exp(-i J_e dt (XX+YY+ZZ)) by the
+    matrix exponential, the same coupling on a bond in every layer, the uniform
+    circuit's colour order, and the same draw for the same seed."""
+    lat = w.square(4, 4)
+    dt = 0.2
+    groups = w.disordered_heisenberg_circuit(lat, 2, dt, seed=3)
+    again = w.disordered_heisenberg_circuit(lat, 2, dt, seed=3)
+    uni = w.heisenberg_circuit(lat, 2, dt)
+    Hb = np.kron(X, X) + np.kron(Y, Y) + np.kron(Z, Z)
+    assert len(groups) == len(uni)
+    per_bond = {}
+    for g, gu, ga in zip(groups, uni, again):
+        assert [(a, b) for a, b, _ in g] == [(a, b) for a, b, _ in gu]
+        for (a, b, U), (_, _, Ua) in zip(g, ga):
+            assert np.array_equal(U, Ua)
+            J = -np.angle(U[0, 0]) / dt          # |00> is an eigenvector with phase e^{-i J dt}
+            assert 0.8 <= J <= 1.2
+            assert np.abs(U - scipy.linalg.expm(-1j * J * dt * Hb)).max() < 1e-13
+            if (a, b) in per_bond:
+                assert np.array_equal(per_bond[(a, b)], U)
+            per_bond[(a, b)] = U
+    assert len(per_bond) == len(lat.edges)
+    assert len({round(float(-np.angle(U[0, 0]) / dt), 12) for U in per_bond.values()}) == len(per_bond)
+
+
 def test_givens_is_xx_plus_yy_rotation():
     th = 1.234
     U = w.givens_gate(th)
