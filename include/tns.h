@@ -147,10 +147,14 @@ tns_status tns_sample(tns_state* s, int32_t chi_b, int64_t n_samples, uint64_t s
 /*
  * tns_sample_range -- samples first .. first + n_samples - 1 of the stream that
  * tns_sample draws for this (state, chi_b, seed): output row r holds sample
- * first + r (Philox counter (first + r, q)), bit-identical to row first + r of a
- * tns_sample call with at least first + n_samples samples.  Samples are
- * independent draws, so disjoint ranges shard one stream across devices or calls
- * with no exchange between them.  first < 0 is TNS_ERR_ARG; buffers as tns_sample.
+ * first + r (Philox counter (first + r, q)), equal to row first + r of a
+ * tns_sample call with at least first + n_samples samples: bit-identical in
+ * TNS_PREC_FP64; in TNS_PREC_MIXED the same bits with conditionals and log q equal
+ * to FP32 rounding (a contraction whose rows span the chunk's samples may run on the
+ * tensor cores or the CUDA cores depending on the chunk's size), so bits can differ
+ * only where u and q(0 | prefix) tie to that rounding.  Samples are independent
+ * draws, so disjoint ranges shard one stream across devices or calls with no
+ * exchange between them.  first < 0 is TNS_ERR_ARG; buffers as tns_sample.
  */
 tns_status tns_sample_range(tns_state* s, int32_t chi_b, int64_t first, int64_t n_samples, uint64_t seed,
                             uint8_t* bits_dev, double* logq_dev, double* cond_dev);

@@ -380,6 +380,9 @@ static void swap_roles(GemmParams& p) {
 }
 
 // Stable insertion sort of index groups by the key stride `key`, carrying the other arrays.
+// Reference batch at which the tensor-core operand roles are weighed.
+static constexpr long long TC_ROLE_REF_BATCH = 128;
+
 static void sort_groups(int n, int* dim, long long* key, long long* o1, long long* o2) {
   for (int i = 1; i < n; ++i)
     for (int j = i; j > 0 && key[j] < key[j - 1]; --j) {
@@ -440,7 +443,11 @@ static TcRole tc_role(const GemmParams& p, long long nbatch, bool swapped) {
   r.a_sh = operand_shared(q, 0);
   r.b_sh = operand_shared(q, 1);
   r.ok = !(r.a_sh && r.b_sh && nbatch > 1);
-  const double rowsA = (double)(r.a_sh ? 1 : nbatch) * q.M, rowsB = (double)(r.b_sh ? 1 : nbatch) * q.N;
+  // the packing cost is weighed at a fixed reference batch, not the call's: the role
+  // decides which operand's rounding is split, so it must not change with the number
+  // of batch entries (a sample drawn in a chunk of any size gets the same bits)
+  const double nref = (double)TC_ROLE_REF_BATCH;
+  const double rowsA = (r.a_sh ? 1.0 : nref) * q.M, rowsB = (r.b_sh ? 1.0 : nref) * q.N;
   r.cost = rowsA * q.K * (r.ad ? 0.0 : 8.0) + rowsB * q.K * 32.0;
   return r;
 }
@@ -458,9 +465,13 @@ static bool pick_role(const GemmParams& p0, long long nbatch, TcRole& r) {
 }
 
 // Whether a contraction of this size goes to the tensor cores (else the SIMT kernel).
+// Decided per batch entry (2^18 MACs, i.e. 2^24 at the reference batch of 64 entries),
+// never by the batch count: the two paths round differently, and a batch entry's
+// result must not depend on how many entries share its launch.
 static bool tc_worth_it(const GemmParams& p, long long nbatch) {
-  const double macs = (double)p.M * (double)p.N * (double)p.K * (double)nbatch;
-  return macs >= 16777216.0 && p.K >= 8;
+  (void)nbatch;
+  const double macs = (double)p.M * (double)p.N * (double)p.K;
+  return macs >= 262144.0 && p.K >= 8;
 }
 
 // Run the contraction on the tensor cores.  *handled = false (and nothing
@@ -709,11 +720,15 @@ cudaError_t contract(const TView& A, const TView& B, const TView& C, Prec prec, 
   long long gx = (p.M + 63) / 64;
   int gy = (p.N + 63) / 64;
   if (gx > 2147483647LL || gy > 65535) return cudaErrorInvalidValue;
-  // split K when the output has too few tiles to fill the GPU
+  // split K when one batch entry's output has too few tiles to fill the GPU.  The
+  // split count sets the summation order, so it follows the entry's shape only (at most
+  // 15 splits: grids of up to 4096 entries fit), never the batch count; only batches
+  // beyond 65535 / 15 entries cap it further.
   const long long tiles = gx * gy * nbatch;
+  const long long tiles_e = gx * gy;
   int splits = 1;
-  if (tiles < 2 * 152 && p.K >= 1024) {
-    splits = (int)std::min<long long>(std::min<long long>(64, p.K / 512), (4 * 152 + tiles - 1) / tiles);
+  if (tiles_e < 2 * 152 && p.K >= 1024) {
+    splits = (int)std::min<long long>(std::min<long long>(15, p.K / 512), (4 * 152 + tiles_e - 1) / tiles_e);
     splits = std::max(1, std::min<int>(splits, (int)(65535 / std::max<long long>(1, nbatch))));
   }
   const int bk = (prec == Prec::F32) ? 16 : 8;

@@ -465,8 +465,9 @@ static cudaError_t pgram(tns_state* s, Prec p, const void* Y, long long S, long 
   if (p == Prec::F64 || n > GRAM_MAX_N || S > 65535)
     return pcontract(s, PC_ZIP, view(const_cast<void*>(Y), "Smc", {S, M, n}, true),
                      view(const_cast<void*>(Y), "Sme", {S, M, n}), view(G, "Sce", {S, n, n}), p);
-  // enough blocks for several per SM, each with at least 128 rows
-  int splits = (int)std::max<long long>(1, std::min<long long>((M + 127) / 128, (4 * 152 + S - 1) / S));
+  // row splits from the panel height only (at least 256 rows each, at most 8): the
+  // split sets the summation order, which must not depend on the chunk size
+  int splits = (int)std::max<long long>(1, std::min<long long>((M + 255) / 256, 8));
   const long long rows_per = (M + splits - 1) / splits;
   splits = (int)((M + rows_per - 1) / rows_per);
   cudaEvent_t ev = s->prof.begin(s->st);

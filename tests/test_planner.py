@@ -57,12 +57,22 @@ def test_two_batch_groups(lib):
     assert d["tc"] == 1 and d["a_in_place"] == 1 and d["batch"] == S * P and d["tile_n"] == 128
 
 
-def test_small_contractions_stay_on_cuda_cores(lib):
+def test_path_choice_is_per_batch_entry(lib):
+    """Tensor cores or CUDA cores by the MACs of one batch entry (at least 2^18), never by
+    the batch count: the two paths round differently, and a sample's result must not
+    depend on the size of the chunk it is drawn in."""
     n = 72
-    d = plan(lib, view("Smc", (1, 2048, n)), view("Sme", (1, 2048, n)), view("Sce", (1, n, n)), conj_a=1)
-    assert d["tc"] == 0 and d["M"] * d["N"] * d["K"] * d["batch"] < 2 ** 24
-    d = plan(lib, view("Smc", (S, 2048, n)), view("Sme", (S, 2048, n)), view("Sce", (S, n, n)), conj_a=1)
-    assert d["tc"] == 1 and d["tile_n"] == 256 and d["a_in_place"] == 0      # conjugated A is gathered
+    for batch in (1, 7, S):
+        d = plan(lib, view("Smc", (batch, 2048, n)), view("Sme", (batch, 2048, n)), view("Sce", (batch, n, n)),
+                 conj_a=1)
+        assert d["tc"] == 1 and d["tile_n"] == 256 and d["a_in_place"] == 0  # conjugated A is gathered
+        d = plan(lib, view("Smc", (batch, 32, 64)), view("Sme", (batch, 32, 64)), view("Sce", (batch, 64, 64)),
+                 conj_a=1)
+        assert d["tc"] == 0 and d["M"] * d["N"] * d["K"] < 2 ** 18
+    # the operand roles do not follow the batch count either
+    roles = {plan(lib, view("Smk", (b, 4096, 512)), view("Snk", (b, 256, 512), shared="S"),
+                  view("Smn", (b, 4096, 256)))["swapped"] for b in (2, 7, S)}
+    assert len(roles) == 1
 
 
 def test_shared_operand_goes_to_the_expanded_side_and_rows_merge(lib):
