@@ -301,9 +301,10 @@ tns_status tns_profile_read(tns_state* s, int32_t kernel_class, double* device_m
  *   cuda_stream  stream to launch on; the call returns after the launch and the
  *              results are ready when the stream reaches that point
  * Scratch: a static 16 MiB device array per GPU that loads the library, held
- * until the process exits.  It holds 4 bytes per matrix plus, when 2*n'^2*16
- * bytes (n' = n rounded up to even) exceed 200 KiB of shared memory, that much
- * per matrix; a batch needing more than 16 MiB returns TNS_ERR_ARG.  Every call
+ * until the process exits.  It holds 4 bytes per matrix plus, when the
+ * eigensolver's shared-memory working copy, 2*n'*(n'+1)*16 bytes (n' = n rounded
+ * up to even), exceeds 200 KiB, a global working copy of 2*n'^2*16 bytes per
+ * matrix; a batch needing more than 16 MiB returns TNS_ERR_ARG.  Every call
  * shares the one array, so calls that overlap on the GPU (different streams,
  * or threads using one device) race: order them on one stream.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress)
